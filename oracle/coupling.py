@@ -1,0 +1,122 @@
+"""Coupling operators for immersed particles (FP64).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Coupling force over a (sub-)step of length s, particle i with velocity v,
+interpolated fluid velocity u, intrinsic force F_int, mass m, reference
+density rho0 (a = 1):
+
+  force coupling, Crank-Nicolson midpoint force      Sec. 5.2, Eq. [modified-force]
+      alpha = gamma s / m, beta = gamma s / rho0, D = 1 + alpha/2 + beta/2
+      F^h = -[gamma (v - u) + (alpha/2) F_int] / D       (zeta = 0)
+  original external boundary force                   Sec. 5.3, Eq. [ebf]
+      force coupling with gamma = rho0 a^3 / h
+  modified external boundary force                   Sec. 5.3, Eq. [modified-ebf]
+      F^h = -gamma/(alpha+beta) (v - u) - alpha/(alpha+beta) F_int
+          = -(v - u) / (s (1/m + 1/rho0)) - r F_int,  r = 1/(1 + m/rho0)
+      (r is the immersion number of Eq. [immersion]; gamma cancels)
+  first-order force coupling (the P S C F scheme)    Sec. 5.2
+      F^h = -gamma (v - u)     (u held constant over the step)
+
+A force half-step F^1/2 is the same formula with s = h/2 (Sec. 5.2, "a
+half-step is achieved by substituting h by h/2").  The particle is then
+kicked with v += (s/m)(F^h + F_int) (Alg. 3 writes dt/2 and drops 1/m_i;
+read as the Newton equation of Sec. 5.2) and the fluid receives -F^h through
+the spreading operator.
+
+Intrinsic forces (the paper's CalculateForces, Alg. 2/3) are model input;
+provided here: harmonic bonds U = k/2 (|d| - r0)^2 between listed pairs
+(minimum-image distance on periodic axes) and a constant external force per
+particle.  Both are pairwise or external, so sum F_int has no internal part.
+"""
+import numpy as np
+
+KINDS = ('none', 'ibm', 'fc', 'ebf', 'mebf')
+
+
+def wrap_positions(pos, shape, walls):
+    """Wrap x, y (and z unless walls) into [0, n): r = fmod(X, n), +n if < 0,
+    -n if the result rounded up to n."""
+    nz, ny, nx = shape
+    out = pos.copy()
+    for a, n in enumerate((nx, ny, nz)):
+        if a == 2 and walls:
+            continue
+        r = np.fmod(out[:, a], n)
+        r = np.where(r < 0.0, r + n, r)
+        r = np.where(r >= n, r - n, r)
+        out[:, a] = r
+    return out
+
+
+def min_image(d, shape, walls):
+    nz, ny, nx = shape
+    out = d.copy()
+    for a, n in enumerate((nx, ny, nz)):
+        if a == 2 and walls:
+            continue
+        out[:, a] = out[:, a] - n * np.rint(out[:, a] / n)
+    return out
+
+
+class Particles:
+    """Lagrangian points: positions, velocities, masses, bonds, external force."""
+
+    def __init__(self, pos, vel=None, mass=None, bonds=None, bond_k=None,
+                 bond_r0=None, ext_force=None):
+        self.pos = np.array(pos, dtype=np.float64).reshape(-1, 3)
+        M = self.pos.shape[0]
+        self.vel = np.zeros((M, 3)) if vel is None else \
+            np.array(vel, dtype=np.float64).reshape(M, 3)
+        self.mass = np.ones(M) if mass is None else \
+            np.array(mass, dtype=np.float64).reshape(M)
+        self.bonds = np.zeros((0, 2), dtype=np.int64) if bonds is None else \
+            np.array(bonds, dtype=np.int64).reshape(-1, 2)
+        nb = self.bonds.shape[0]
+        self.bond_k = np.zeros(nb) if bond_k is None else \
+            np.broadcast_to(np.asarray(bond_k, dtype=np.float64), (nb,)).copy()
+        self.bond_r0 = np.zeros(nb) if bond_r0 is None else \
+            np.broadcast_to(np.asarray(bond_r0, dtype=np.float64), (nb,)).copy()
+        self.ext_force = np.zeros((M, 3)) if ext_force is None else \
+            np.array(ext_force, dtype=np.float64).reshape(M, 3)
+
+    def copy(self):
+        return Particles(self.pos, self.vel, self.mass, self.bonds, self.bond_k,
+                         self.bond_r0, self.ext_force)
+
+
+def intrinsic_forces(parts, pos, shape, walls):
+    """F_int(X): harmonic bonds plus constant external forces."""
+    F = parts.ext_force.copy()
+    if parts.bonds.shape[0]:
+        i, j = parts.bonds[:, 0], parts.bonds[:, 1]
+        d = min_image(pos[j] - pos[i], shape, walls)
+        dist = np.sqrt((d * d).sum(axis=1))
+        mag = parts.bond_k * (dist - parts.bond_r0) / dist
+        fij = d * mag[:, None]             # force on i, pulling towards j
+        np.add.at(F, i, fij)
+        np.add.at(F, j, -fij)
+    return F
+
+
+def coupling_force(kind, order, v, u, Fint, mass, s, gamma, rho0,
+                   include_int=True):
+    """Hydrodynamic force F^h on each particle for a (sub-)step of length s.
+
+    kind in ('fc', 'ebf', 'mebf'); v, u, Fint (M, 3); mass (M,).
+    include_int=False gives the coupling-only operator F_h of the split in
+    Sec. 6 (intrinsic forces integrated separately).
+    """
+    m = mass[:, None]
+    Fi = Fint if include_int else np.zeros_like(Fint)
+    if kind == 'ebf':
+        gamma = rho0 / 1.0          # gamma = rho a^3 / h with a = h = 1
+    if kind == 'mebf':
+        r = 1.0 / (1.0 + m / rho0)
+        return -(v - u) / (s * (1.0 / m + 1.0 / rho0)) - r * Fi
+    if order == 1:
+        return -gamma * (v - u)
+    alpha = gamma * s / m
+    beta = gamma * s / rho0
+    D = 1.0 + 0.5 * alpha + 0.5 * beta
+    return -(gamma * (v - u) + 0.5 * alpha * Fi) / D
