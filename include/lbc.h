@@ -1,0 +1,224 @@
+/*
+ * lbc.h -- C ABI of the GB300 coupled lattice-Boltzmann library.
+ *
+ * One library call advances a box of D3Q19 lattice-Boltzmann fluid coupled to
+ * Lagrangian particles with the second-order operator splitting of
+ * U. D. Schiller, "A unified operator splitting approach for multi-scale
+ * fluid-particle coupling in the lattice Boltzmann method" (arXiv:1406.2211).
+ * The problem statement follows the paper: a lattice with relaxation
+ * (Sec. 3.2, Eqs. [collision-operator], [mrt-coll]), a set of Lagrangian
+ * points with masses (Sec. 5.2), a coupling kind with its parameters gamma,
+ * m, rho, a, h (Sec. 5.2 Eq. [modified-force], Sec. 5.3 Eqs. [ebf],
+ * [modified-ebf], [immersion]), an interpolation kernel (App. A) and a step
+ * count.  Lattice units: h = a = 1, c_s^2 = 1/3.
+ *
+ * Conventions
+ *  - Device memory is owned by the caller.  lbc_box_bytes_required() states
+ *    how many bytes one box needs; the caller allocates them (for example as
+ *    a torch uint8 tensor) and hands the pointer to lbc_box_create().  The
+ *    library never allocates or frees device memory.  The box handle itself
+ *    is a small host object freed by lbc_box_destroy().
+ *  - Host arrays passed in are read during the call only; the caller keeps
+ *    ownership.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return; getters (lbc_box_get_*,
+ *    lbc_box_invariants) synchronise that stream before returning.
+ *  - Errors are returned as lbc_status codes; no C++ exception crosses this
+ *    interface.  A device-detected error (non-finite density found by
+ *    lbc_box_invariants) is latched in the box and returned by
+ *    lbc_box_status() and by every later lbc_box_step().
+ *  - Layouts: cell (x, y, z) sits at position (x, y, z); fields are dense
+ *    with x fastest: rho[(z*ny + y)*nx + x], u[c][(z*ny + y)*nx + x] with
+ *    c = 0, 1, 2 for (x, y, z).  Populations: f[i][z][y][x] in the D3Q19
+ *    order rest, +x, -x, +y, -y, +z, -z, (+x+y), (-x-y), (+x-y), (-x+y),
+ *    (+x+z), (-x-z), (+x-z), (-x+z), (+y+z), (-y-z), (+y-z), (-y+z).
+ *    Particle arrays are [n][3] (x, y, z per particle).
+ *  - A box is not thread safe; different boxes may be used concurrently.
+ */
+#ifndef LBC_H
+#define LBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lbc_status;
+#define LBC_OK 0
+#define LBC_ERR_ARG (-1)         /* invalid argument or descriptor */
+#define LBC_ERR_OOM (-2)         /* caller memory too small */
+#define LBC_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define LBC_ERR_NONFINITE (-4)   /* non-finite density detected (latched) */
+#define LBC_ERR_TIMEOUT (-5)     /* reserved: bounded device wait expired */
+#define LBC_ERR_STATE (-6)       /* call not valid in the box's state */
+#define LBC_ERR_UNSUPPORTED (-7) /* valid but not implemented combination */
+
+/* collision models (Sec. 3.2) */
+#define LBC_BGK 0
+#define LBC_MRT 1
+/* population storage: FP64, FP32, or 16-bit deviations from the rest
+ * equilibrium w_i rho0 (IEEE half or bfloat16), arithmetic in FP32 */
+#define LBC_F64 0
+#define LBC_F32 1
+#define LBC_F16_DEV 2
+#define LBC_BF16_DEV 3
+/* coupling kinds (Sec. 5) */
+#define LBC_NONE 0
+#define LBC_IBM 1   /* immersed boundary method, Sec. 5.1 */
+#define LBC_FC 2    /* viscous force coupling, Sec. 5.2 */
+#define LBC_EBF 3   /* original external boundary force, gamma = rho0 a^3/h */
+#define LBC_MEBF 4  /* modified external boundary force, Sec. 5.3 */
+/* interpolation / spreading kernels phi (App. A) */
+#define LBC_TRILINEAR 0
+#define LBC_PESKIN4 1
+#define LBC_PESKIN3 2
+/* time-step splittings for force-coupled particles */
+#define LBC_SPLIT_BASE 0    /* P^1/2 F^1/2 (C^1/2 S C^1/2) F^1/2 P^1/2, Eq. [fc-splitting] */
+#define LBC_SPLIT_INSIDE 1  /* [P^1/4n F^1/2n P^1/4n]^n LB [..]^n, Eq. [multistep] */
+#define LBC_SPLIT_OUTSIDE 2 /* F_h^1/2 [P F_int P]^n LB [P F_int P]^n F_h^1/2, Sec. 6 */
+
+typedef struct lbc_lattice_desc {
+  int32_t nx, ny, nz;        /* cells; periodic in x and y; z periodic or walls */
+  int32_t collision;         /* LBC_BGK or LBC_MRT */
+  double tau;                /* lattice relaxation time: shear rate 1/tau,
+                                nu = (tau - 1/2)/3 */
+  double mrt_lambda[4];      /* MRT full-step rates (shear, bulk, odd ghosts,
+                                even ghosts); 0 = default: shear = 1/tau,
+                                bulk = shear, ghosts = 1 */
+  double rho0;               /* reference density; rho in beta = gamma h/(rho a^3) */
+  double body_force[3];      /* uniform body-force density g */
+  int32_t z_walls;           /* 0 periodic in z; 1 halfway bounce-back walls
+                                at z = -1/2 and z = nz - 1/2 */
+  double wall_velocity[2][3];/* bottom and top wall velocity */
+  int32_t storage;           /* LBC_F64, LBC_F32, LBC_F16_DEV, LBC_BF16_DEV */
+  double storage_scale;      /* 16-bit forms store dev/(w_i*scale); 0 = 1 */
+} lbc_lattice_desc;
+
+typedef struct lbc_coupling_desc {
+  int32_t kind;              /* LBC_NONE, LBC_IBM, LBC_FC, LBC_EBF, LBC_MEBF */
+  int32_t order;             /* 2: the paper's split schemes; 1: first-order
+                                P S C F scheme */
+  int32_t stencil;           /* LBC_TRILINEAR, LBC_PESKIN4, LBC_PESKIN3 */
+  double gamma;              /* friction of force coupling (LBC_FC) */
+  int32_t split;             /* LBC_SPLIT_BASE / _INSIDE / _OUTSIDE (order 2,
+                                force-coupled kinds; IBM uses BASE) */
+  int32_t substeps;          /* n >= 1 of the multiple-time-step splits */
+} lbc_coupling_desc;
+
+typedef struct lbc_particles_desc {
+  int64_t n;                 /* number of particles / markers */
+  const double* pos;         /* [n][3] positions, lattice units */
+  const double* vel;         /* [n][3] velocities (NULL = 0; unused for IBM) */
+  const double* mass;        /* [n] masses (NULL = 1; unused for IBM) */
+  const double* ext_force;   /* [n][3] constant external force (NULL = 0),
+                                part of the intrinsic force F_int */
+  int64_t nbonds;            /* harmonic bonds U = k/2 (|r_j - r_i| - r0)^2 */
+  const int32_t* bond_ij;    /* [nbonds][2] particle indices */
+  const double* bond_k;      /* [nbonds] spring constants */
+  const double* bond_r0;     /* [nbonds] rest lengths */
+} lbc_particles_desc;
+
+typedef struct lbc_box lbc_box;
+
+/* ABI version of this header (increments on incompatible change). */
+int32_t lbc_abi_version(void);
+
+/* sizeof of the three descriptor structs (lattice, coupling, particles),
+ * written to out[0..2]; lets a binding check its struct layout. */
+void lbc_desc_sizes(size_t out[3]);
+
+/* Human-readable name of a status code (static string). */
+const char* lbc_status_string(lbc_status s);
+
+/* Bytes of caller-provided device memory one box needs for the given
+ * descriptors and maximum particle / bond counts.  Writes *bytes.
+ * Returns LBC_ERR_ARG for invalid descriptors. */
+lbc_status lbc_box_bytes_required(const lbc_lattice_desc* lat,
+                                  const lbc_coupling_desc* cpl,
+                                  int64_t max_particles, int64_t max_bonds,
+                                  size_t* bytes);
+
+/* Create a box in caller memory `arena_dev` (device pointer, at least
+ * lbc_box_bytes_required() bytes, 256-byte aligned).  The fluid starts at
+ * rest with density rho0 and no particles.  *out receives the handle.
+ * Errors: LBC_ERR_ARG (descriptor), LBC_ERR_OOM (arena too small),
+ * LBC_ERR_CUDA. */
+lbc_status lbc_box_create(const lbc_lattice_desc* lat,
+                          const lbc_coupling_desc* cpl, int64_t max_particles,
+                          int64_t max_bonds, void* arena_dev,
+                          size_t arena_bytes, void* stream, lbc_box** out);
+
+/* Free the host handle (the caller frees the arena afterwards).  Waits for
+ * the box's captured graphs to be released. */
+lbc_status lbc_box_destroy(lbc_box* box);
+
+/* Set the fluid to the equilibrium f^eq(rho, u) of a uniform state, clear
+ * the pending force of the previous half step. */
+lbc_status lbc_box_init_equilibrium(lbc_box* box, double rho,
+                                    const double u[3], void* stream);
+
+/* Set the fluid to f^eq(rho(x), u(x)) from host fields rho[N], u[3][N]. */
+lbc_status lbc_box_set_fields(lbc_box* box, const double* rho_host,
+                              const double* u_host, void* stream);
+
+/* Set / get the post-streaming populations fbar (full values, not
+ * deviations) as host FP64 arrays [19][nz][ny][nx] (Sec. 4: the
+ * populations after S and before the closing half collision).  Setting
+ * clears the pending force. */
+lbc_status lbc_box_set_populations(lbc_box* box, const double* fbar_host,
+                                   void* stream);
+lbc_status lbc_box_get_populations(lbc_box* box, double* fbar_host,
+                                   void* stream);
+
+/* Set the pending force density F_a of the previous closing half step
+ * (host FP64 [3][N]; NULL clears it).  For tests of the force path. */
+lbc_status lbc_box_set_pending_force(lbc_box* box, const double* Fa_host,
+                                     void* stream);
+
+/* Upload particles (copied in; counts must not exceed the maxima given at
+ * creation).  Positions are wrapped into the periodic box. */
+lbc_status lbc_box_set_particles(lbc_box* box, const lbc_particles_desc* p,
+                                 void* stream);
+
+/* Advance nsteps time steps (enqueue only).  Steps after the first run as
+ * replays of a captured two-step CUDA graph unless graphs are disabled. */
+lbc_status lbc_box_step(lbc_box* box, int64_t nsteps, void* stream);
+
+/* Physical density and velocity (host FP64 rho[N], u[3][N]); the velocity
+ * includes the pending half force, rho u = sum fbar c + (h/2)(F_a + g)
+ * (Sec. 4).  Either pointer may be NULL. */
+lbc_status lbc_box_get_fields(lbc_box* box, double* rho_host, double* u_host,
+                              void* stream);
+
+/* Particle positions, velocities and last hydrodynamic force F^h (host
+ * [n][3] each, any may be NULL).  For IBM, force_h is the spread force. */
+lbc_status lbc_box_get_particles(lbc_box* box, double* pos, double* vel,
+                                 double* force_h, void* stream);
+
+/* FP64 invariants: total fluid mass, total physical momentum of fluid plus
+ * particles (momentum[3]); latches LBC_ERR_NONFINITE if any density is
+ * non-finite. */
+lbc_status lbc_box_invariants(lbc_box* box, double* mass, double* momentum,
+                              void* stream);
+
+/* Latched device status of the box (LBC_OK or the first error seen). */
+lbc_status lbc_box_status(const lbc_box* box);
+
+/* Options: LBC_OPT_GRAPHS (1 = capture steps in CUDA graphs, default 1). */
+#define LBC_OPT_GRAPHS 1
+lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
+
+/* Number of kernel launches one time step enqueues for this box (for
+ * launch accounting). */
+int64_t lbc_box_launches_per_step(const lbc_box* box);
+
+/* Bytes of one population array (for bandwidth accounting). */
+size_t lbc_box_population_bytes(const lbc_box* box);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBC_H */

@@ -1,0 +1,436 @@
+// Fused lattice-Boltzmann step and population I/O kernels.
+//
+// One time step of the collide-stream-collide scheme with the paper's
+// symmetric force half steps, F^1/2 C^1/2 S C^1/2 F^1/2 (Sec. 4,
+// Eqs. [force-second-halfstep]-[force-first-halfstep]), evaluated in the
+// exactly recombined form: every half force step only shifts the equilibrium
+// velocity (midpoint-velocity Hermite force term), so the two half
+// collisions around it merge into the full collision (1 - Lambda) =
+// (1 - Lambda_1/2)^2 about a shifted equilibrium:
+//
+//   f*_i(x) = f_i^eq(rho, u1) + [(1 - Lambda)(fbar - f^eq(rho, u0))]_i
+//   u0 = sum_i fbar_i c_i / rho,  u1 = u0 + (ca F_a + cb F_b + cg g) / rho
+//
+// with ca = cb = h/2, cg = h for the second-order schemes and ca = 0,
+// cb = cg = h for the first-order P S C F schemes.  BGK: (1 - Lambda) =
+// 1 - 1/tau on every non-conserved moment; MRT: diagonal in the moment basis
+// of lbc_common.cuh (Sec. 3.2, Eq. [mrt-coll]).
+//
+// Memory: two population arrays (A-B), SoA, pull streaming: the kernel for
+// cell x reads f*_i(x - c_i) of the previous step (unaligned by one element
+// for the x-links, still fully coalesced) and writes f*_i(x) of this step
+// (aligned).  The stored quantity is the deviation from the rest
+// equilibrium, f_i - w_i rho0, which keeps FP32 storage accurate at small
+// Mach number.  Walls: halfway bounce-back at z = -1/2 and nz - 1/2 with the
+// moving-wall term (not part of the paper).
+#include "lb_device.cuh"
+
+namespace lbc {
+
+// E_i(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 u.u   (f_i^eq = w_i rho (1 + E_i(u)))
+template <typename C, int I>
+__device__ inline C eq_poly(C ux, C uy, C uz, C uu) {
+  constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+  C cu = C(0);
+  if (cx) cu += C(cx) * ux;
+  if (cy) cu += C(cy) * uy;
+  if (cz) cu += C(cz) * uz;
+  return cu * (C(3) + C(4.5) * cu) - C(1.5) * uu;
+}
+
+template <typename C, int I = 0>
+__device__ inline void eq_all(C ux, C uy, C uz, C (&e)[Q]) {
+  if constexpr (I < Q) {
+    e[I] = eq_poly<C, I>(ux, uy, uz, ux * ux + uy * uy + uz * uz);
+    eq_all<C, I + 1>(ux, uy, uz, e);
+  }
+}
+
+// m_k = sum_i e_ki v_i for one moment (compile-time coefficients)
+template <typename C, int K, int I = 0>
+__device__ inline C moment(const C (&v)[Q]) {
+  if constexpr (I == Q) {
+    return C(0);
+  } else {
+    constexpr int e = mrt_e(K, I);
+    C rest = moment<C, K, I + 1>(v);
+    if constexpr (e == 0) return rest;
+    else if constexpr (e == 1) return v[I] + rest;
+    else if constexpr (e == -1) return rest - v[I];
+    else return C(e) * v[I] + rest;
+  }
+}
+
+// out_i += w_i sum_{k=4..18} e_ki m_k   (m_k already scaled by gamma_k / b_k)
+template <typename C, int I, int K = 4>
+__device__ inline C back(const C (&m)[Q]) {
+  if constexpr (K == Q) {
+    return C(0);
+  } else {
+    constexpr int e = mrt_e(K, I);
+    C rest = back<C, I, K + 1>(m);
+    if constexpr (e == 0) return rest;
+    else if constexpr (e == 1) return m[K] + rest;
+    else if constexpr (e == -1) return rest - m[K];
+    else return C(e) * m[K] + rest;
+  }
+}
+
+template <typename C, int K = 4>
+__device__ inline void moments_all(const C (&neq)[Q], const C (&gk)[5], C (&m)[Q]) {
+  if constexpr (K < Q) {
+    constexpr double invb = 1.0 / mrt_b(K);
+    m[K] = moment<C, K>(neq) * (gk[mrt_group(K)] * C(invb));
+    moments_all<C, K + 1>(neq, gk, m);
+  }
+}
+
+template <typename C, int I = 0>
+__device__ inline void back_all(const C (&m)[Q], C (&post)[Q]) {
+  if constexpr (I < Q) {
+    post[I] = C(w_of(I)) * back<C, I>(m);
+    back_all<C, I + 1>(m, post);
+  }
+}
+
+template <typename S, int COLL, bool WALLS, bool FORCED>
+__global__ void __launch_bounds__(256)
+lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+
+  C f[Q];
+  pull_cell<S, WALLS>(fin, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+
+  C rd = C(0), jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rd += f[i];
+    if (cx_of(i)) jx += C(cx_of(i)) * f[i];
+    if (cy_of(i)) jy += C(cy_of(i)) * f[i];
+    if (cz_of(i)) jz += C(cz_of(i)) * f[i];
+  }
+  const C rho = C(a.rho0) + rd;
+  const C inv = C(1) / rho;
+  const C u0x = jx * inv, u0y = jy * inv, u0z = jz * inv;
+  C Fx = C(a.cg * a.gvec[0]), Fy = C(a.cg * a.gvec[1]), Fz = C(a.cg * a.gvec[2]);
+  if (FORCED) {
+    const int t = tile_of(g, x, y, z);
+    if (a.Fa && a.flag_a[t]) {
+      Fx += C(a.ca) * C(a.Fa[cell]);
+      Fy += C(a.ca) * C(a.Fa[g.qstride + cell]);
+      Fz += C(a.ca) * C(a.Fa[2 * g.qstride + cell]);
+    }
+    if (a.Fb && a.flag_b[t]) {
+      Fx += C(a.cb) * C(a.Fb[cell]);
+      Fy += C(a.cb) * C(a.Fb[g.qstride + cell]);
+      Fz += C(a.cb) * C(a.Fb[2 * g.qstride + cell]);
+    }
+  }
+  const C u1x = u0x + Fx * inv, u1y = u0y + Fy * inv, u1z = u0z + Fz * inv;
+
+  C e0[Q], e1[Q];
+  eq_all<C>(u0x, u0y, u0z, e0);
+  eq_all<C>(u1x, u1y, u1z, e1);
+
+  if (COLL == 0) {
+    const C gam = C(a.gamma_bgk);
+    const C omg = C(1) - gam;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const C wi = C(w_of(i));
+      const C v = gam * f[i] + wi * (omg * rd + rho * (e1[i] - gam * e0[i]));
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+    }
+  } else {
+    C neq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) neq[i] = f[i] - C(w_of(i)) * (rd + rho * e0[i]);
+    const C gk[5] = {C(0), C(a.gamma_k[0]), C(a.gamma_k[1]), C(a.gamma_k[2]), C(a.gamma_k[3])};
+    C m[Q];
+    moments_all<C>(neq, gk, m);
+    C post[Q];
+    back_all<C>(m, post);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const C v = C(w_of(i)) * (rd + rho * e1[i]) + post[i];
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+    }
+  }
+}
+
+static dim3 cell_grid(const Geom& g, int* bx) {
+  int b = ((g.nx + 31) / 32) * 32;
+  if (b > 256) b = 256;
+  *bx = b;
+  return dim3((g.nx + b - 1) / b, g.ny, g.nz);
+}
+
+template <typename S>
+static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream_t s) {
+  int bx;
+  dim3 grid = cell_grid(a.g, &bx);
+  const bool forced = a.Fa != nullptr || a.Fb != nullptr;
+  const S* in = static_cast<const S*>(fin);
+  S* out = static_cast<S*>(fout);
+#define LBC_LAUNCH(COLL, W, F) lb_step_kernel<S, COLL, W, F><<<grid, bx, 0, s>>>(in, out, a)
+  if (a.collision == 0) {
+    if (a.g.walls) { if (forced) LBC_LAUNCH(0, true, true); else LBC_LAUNCH(0, true, false); }
+    else { if (forced) LBC_LAUNCH(0, false, true); else LBC_LAUNCH(0, false, false); }
+  } else {
+    if (a.g.walls) { if (forced) LBC_LAUNCH(1, true, true); else LBC_LAUNCH(1, true, false); }
+    else { if (forced) LBC_LAUNCH(1, false, true); else LBC_LAUNCH(1, false, false); }
+  }
+#undef LBC_LAUNCH
+}
+
+void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: lb_dispatch<double>(fin, fout, a, s); break;
+    case ST_F32: lb_dispatch<float>(fin, fout, a, s); break;
+    case ST_F16: lb_dispatch<__half>(fin, fout, a, s); break;
+    default: lb_dispatch<__nv_bfloat16>(fin, fout, a, s); break;
+  }
+}
+
+// ------------------------------------------------------------ population I/O
+// fstar_j(y) = fbar_j(y + c_j), or, where y + c_j lies beyond a wall,
+// fbar_opp(j)(y) minus the wall term of opp(j) (inverse of pull_cell).
+template <typename S>
+__global__ void unstream_kernel(const S* __restrict__ fbar, S* __restrict__ fstar, const LBArgs a) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const int zt = z + cz_of(j);
+    C v;
+    if (g.walls && (zt < 0 || zt >= g.nz)) {
+      const int o = opp_of(j);
+      const double bb = zt < 0 ? a.bb_bot[o] : a.bb_top[o];
+      v = Store<S>::load(fbar, o * g.qstride + cell, o, a.scale16) - C(bb);
+    } else {
+      const int xt = wrap_int(x + cx_of(j), g.nx);
+      const int yt = wrap_int(y + cy_of(j), g.ny);
+      const int zz = wrap_int(zt, g.nz);
+      v = Store<S>::load(fbar, j * g.qstride + zz * g.plane + (long long)yt * g.pitch + xt, j, a.scale16);
+    }
+    Store<S>::store(fstar, j * g.qstride + cell, v, j, a.scale16);
+  }
+}
+
+template <typename S>
+__global__ void pull_kernel(const S* __restrict__ fstar, S* __restrict__ fbar, const LBArgs a) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  C f[Q];
+  if (g.walls) pull_cell<S, true>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  else pull_cell<S, false>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Store<S>::store(fbar, i * g.qstride + cell, f[i], i, a.scale16);
+}
+
+// physical density and velocity of every cell (FP64 outputs, dense layout)
+template <typename S>
+__global__ void fields_kernel(const S* __restrict__ fstar, const LBArgs a, double ca, double cg,
+                              double* __restrict__ rho_out, double* __restrict__ u_out) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  const long long dense = ((long long)z * g.ny + y) * g.nx + x;
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  C f[Q];
+  if (g.walls) pull_cell<S, true>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  else pull_cell<S, false>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  double rd = 0, j[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rd += double(f[i]);
+    j[0] += cx_of(i) * double(f[i]);
+    j[1] += cy_of(i) * double(f[i]);
+    j[2] += cz_of(i) * double(f[i]);
+  }
+  const double rho = a.rho0 + rd;
+  const int t = tile_of(g, x, y, z);
+  const bool fa = a.Fa != nullptr && a.flag_a[t];
+  for (int c = 0; c < 3; ++c) {
+    double jj = j[c] + cg * a.gvec[c];
+    if (fa) jj += ca * double(a.Fa[c * g.qstride + cell]);
+    u_out[c * N + dense] = jj / rho;
+  }
+  rho_out[dense] = rho;
+}
+
+constexpr int RED_THREADS = 256;
+
+int invariants_blocks(const Geom& g) {
+  long long rows = (long long)g.ny * g.nz;
+  long long b = (rows + 7) / 8;      // 8 rows per block
+  return (int)(b < 4096 ? b : 4096);
+}
+
+// per block: sum over a strided set of rows of (rho - rho0, j_phys, nonfinite)
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS)
+invariants_kernel(const S* __restrict__ fstar, const LBArgs a, double ca, double cg, double* partial) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  double acc[5] = {0, 0, 0, 0, 0};
+  const long long rows = (long long)g.ny * g.nz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int y = int(r % g.ny), z = int(r / g.ny);
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      C f[Q];
+      if (g.walls) pull_cell<S, true>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+      else pull_cell<S, false>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+      double rd = 0, j0 = 0, j1 = 0, j2 = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double v = double(f[i]);
+        rd += v;
+        j0 += cx_of(i) * v; j1 += cy_of(i) * v; j2 += cz_of(i) * v;
+      }
+      const long long cell = z * g.plane + (long long)y * g.pitch + x;
+      const int t = tile_of(g, x, y, z);
+      if (a.Fa != nullptr && a.flag_a[t]) {
+        j0 += ca * double(a.Fa[cell]);
+        j1 += ca * double(a.Fa[g.qstride + cell]);
+        j2 += ca * double(a.Fa[2 * g.qstride + cell]);
+      }
+      j0 += cg * a.gvec[0]; j1 += cg * a.gvec[1]; j2 += cg * a.gvec[2];
+      acc[0] += rd; acc[1] += j0; acc[2] += j1; acc[3] += j2;
+      if (!isfinite(rd)) acc[4] += 1.0;
+    }
+  }
+  __shared__ double sh[5][RED_THREADS];
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) partial[blockIdx.x * 5 + k] = sh[k][0];
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+final_reduce_kernel(const double* partial, int nblocks, double* out) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < 5; ++k) acc[k] += partial[b * 5 + k];
+  __shared__ double sh[5][RED_THREADS];
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) out[k] = sh[k][0];
+}
+
+template <typename S>
+static void io_dispatch(int which, const void* in, void* out, const LBArgs& a, cudaStream_t s) {
+  int bx;
+  dim3 grid = cell_grid(a.g, &bx);
+  if (which == 0)
+    unstream_kernel<S><<<grid, bx, 0, s>>>(static_cast<const S*>(in), static_cast<S*>(out), a);
+  else
+    pull_kernel<S><<<grid, bx, 0, s>>>(static_cast<const S*>(in), static_cast<S*>(out), a);
+}
+
+void launch_unstream(int storage, const void* fbar, void* fstar, const LBArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: io_dispatch<double>(0, fbar, fstar, a, s); break;
+    case ST_F32: io_dispatch<float>(0, fbar, fstar, a, s); break;
+    case ST_F16: io_dispatch<__half>(0, fbar, fstar, a, s); break;
+    default: io_dispatch<__nv_bfloat16>(0, fbar, fstar, a, s); break;
+  }
+}
+void launch_pull(int storage, const void* fstar, void* fbar, const LBArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: io_dispatch<double>(1, fstar, fbar, a, s); break;
+    case ST_F32: io_dispatch<float>(1, fstar, fbar, a, s); break;
+    case ST_F16: io_dispatch<__half>(1, fstar, fbar, a, s); break;
+    default: io_dispatch<__nv_bfloat16>(1, fstar, fbar, a, s); break;
+  }
+}
+
+void launch_fields(int storage, const void* fstar, const LBArgs& a, double ca, double cg,
+                   double* rho_out, double* u_out, cudaStream_t s) {
+  int bx;
+  dim3 grid = cell_grid(a.g, &bx);
+  switch (storage) {
+    case ST_F64: fields_kernel<double><<<grid, bx, 0, s>>>(static_cast<const double*>(fstar), a, ca, cg, rho_out, u_out); break;
+    case ST_F32: fields_kernel<float><<<grid, bx, 0, s>>>(static_cast<const float*>(fstar), a, ca, cg, rho_out, u_out); break;
+    case ST_F16: fields_kernel<__half><<<grid, bx, 0, s>>>(static_cast<const __half*>(fstar), a, ca, cg, rho_out, u_out); break;
+    default: fields_kernel<__nv_bfloat16><<<grid, bx, 0, s>>>(static_cast<const __nv_bfloat16*>(fstar), a, ca, cg, rho_out, u_out); break;
+  }
+}
+
+void launch_invariants(int storage, const void* fstar, const LBArgs& a, double ca, double cg,
+                       double* partial, double* out, cudaStream_t s) {
+  const int nb = invariants_blocks(a.g);
+  switch (storage) {
+    case ST_F64: invariants_kernel<double><<<nb, RED_THREADS, 0, s>>>(static_cast<const double*>(fstar), a, ca, cg, partial); break;
+    case ST_F32: invariants_kernel<float><<<nb, RED_THREADS, 0, s>>>(static_cast<const float*>(fstar), a, ca, cg, partial); break;
+    case ST_F16: invariants_kernel<__half><<<nb, RED_THREADS, 0, s>>>(static_cast<const __half*>(fstar), a, ca, cg, partial); break;
+    default: invariants_kernel<__nv_bfloat16><<<nb, RED_THREADS, 0, s>>>(static_cast<const __nv_bfloat16*>(fstar), a, ca, cg, partial); break;
+  }
+  final_reduce_kernel<<<1, RED_THREADS, 0, s>>>(partial, nb, out);
+}
+
+// equilibrium post-streaming deviations w_i (rho - rho0) + w_i rho E_i(u)
+template <typename S>
+__global__ void init_eq_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                               S* __restrict__ dst, const LBArgs a, int uniform, double urho,
+                               double ux, double uy, double uz) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  const long long d = ((long long)z * g.ny + y) * g.nx + x;
+  const double r = uniform ? urho : rho[d];
+  const double v0 = uniform ? ux : u[d], v1 = uniform ? uy : u[N + d], v2 = uniform ? uz : u[2 * N + d];
+  const double uu = v0 * v0 + v1 * v1 + v2 * v2;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double cu = cx_of(i) * v0 + cy_of(i) * v1 + cz_of(i) * v2;
+    const double w = w_of(i);
+    const double dev = w * (r - a.rho0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    Store<S>::store(dst, i * g.qstride + cell, typename Store<S>::C(dev), i, a.scale16);
+  }
+}
+
+void launch_init_eq(int storage, const double* rho, const double* u, void* dst, const LBArgs& a,
+                    int uniform, double urho, const double* uv, cudaStream_t s) {
+  int bx;
+  dim3 grid = cell_grid(a.g, &bx);
+  const double ux = uv ? uv[0] : 0.0, uy = uv ? uv[1] : 0.0, uz = uv ? uv[2] : 0.0;
+  switch (storage) {
+    case ST_F64: init_eq_kernel<double><<<grid, bx, 0, s>>>(rho, u, static_cast<double*>(dst), a, uniform, urho, ux, uy, uz); break;
+    case ST_F32: init_eq_kernel<float><<<grid, bx, 0, s>>>(rho, u, static_cast<float*>(dst), a, uniform, urho, ux, uy, uz); break;
+    case ST_F16: init_eq_kernel<__half><<<grid, bx, 0, s>>>(rho, u, static_cast<__half*>(dst), a, uniform, urho, ux, uy, uz); break;
+    default: init_eq_kernel<__nv_bfloat16><<<grid, bx, 0, s>>>(rho, u, static_cast<__nv_bfloat16*>(dst), a, uniform, urho, ux, uy, uz); break;
+  }
+}
+
+}  // namespace lbc

@@ -1,0 +1,136 @@
+// Internal launch interface between the C-ABI layer (lbc_api.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbc_common.cuh"
+
+namespace lbc {
+
+enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// Arguments of the fused LB step (all scalars in double; each kernel
+// converts to its compute type).
+struct LBArgs {
+  Geom g;
+  int collision;          // 0 BGK, 1 MRT
+  double rho0;
+  double gamma_bgk;       // 1 - 1/tau
+  double gamma_k[4];      // MRT 1 - lambda: bulk, shear, odd ghost, even ghost
+  double ca, cb, cg;      // u1 = u0 + (ca F_a + cb F_b + cg g) / rho
+  double gvec[3];         // uniform body force density g
+  double bb_bot[Q];       // moving-wall term of population i arriving from
+  double bb_top[Q];       //   the bottom / top wall: 6 w_i rho0 c_i . u_w
+  // sparse force fields (may be null): F[c * qstride + cell], flags per tile
+  const float* Fa; const uint8_t* flag_a;
+  const float* Fb; const uint8_t* flag_b;
+  float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
+};
+
+void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,
+                    cudaStream_t s);
+// fbar (post-streaming deviations) -> stored pre-streaming form, and back
+void launch_unstream(int storage, const void* fbar, void* fstar, const LBArgs& a,
+                     cudaStream_t s);
+void launch_pull(int storage, const void* fstar, void* fbar, const LBArgs& a,
+                 cudaStream_t s);
+// physical fields: rho, u = (j + ca_phys F_a + cg_phys g) / rho (dense x-fastest)
+void launch_fields(int storage, const void* fstar, const LBArgs& a,
+                   double ca_phys, double cg_phys, double* rho_out,
+                   double* u_out, cudaStream_t s);
+// equilibrium fbar (deviations) from FP64 fields rho[N], u[3][N] (dense) or
+// from a uniform state, written into dst
+void launch_init_eq(int storage, const double* rho, const double* u, void* dst,
+                    const LBArgs& a, int uniform, double urho, const double* uvec,
+                    cudaStream_t s);
+// fluid invariants: partial sums per block then one final block.
+// out[0] = sum of density deviations, out[1..3] = physical momentum,
+// out[4] = number of non-finite densities
+int invariants_blocks(const Geom& g);
+void launch_invariants(int storage, const void* fstar, const LBArgs& a,
+                       double ca_phys, double cg_phys, double* partial,
+                       double* out, cudaStream_t s);
+
+// ------------------------------------------------------------ particles
+struct StencilRec {          // one marker's stencil, sorted order, 80 bytes
+  int bx, by, bz, kind;      // base node per axis; stencil kind
+  float wx[4], wy[4], wz[4]; // 1-D weights of the nodes base + k
+  float F[3];                // force to spread (already signed and weighted)
+  float pad;
+};
+
+struct PartArgs {
+  Geom g;
+  long long M;
+  int stencil;          // 0 trilinear, 1 Peskin 4-point, 2 three-point
+  int S;                // nodes per axis: 2, 4, 3
+};
+
+// drift / intrinsic force / kick / drift sub-step (see particle_kernels.cu)
+struct DriftArgs {
+  double dt_pre, dt_kick, dt_post;
+  int compute_force;     // evaluate F_int at the pre-drifted positions
+  int write_key;         // tile key of the final positions
+  const double* pos_in; const double* vel_in;   // [3][M]
+  double* pos_out; double* vel_out;             // may alias nothing
+  double* fint_out;                              // [3][M] or null
+  uint32_t* key_out; uint32_t* idx_out;
+  const double* mass; const double* ext;        // ext [3][M] or null
+  const int* nbr_start; const int* nbr_j;
+  const double* nbr_k; const double* nbr_r0;
+};
+void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
+
+// LSD radix sort of (key, idx) pairs; ping-pong buffers, result in *_a
+size_t sort_scratch_ints(long long M);
+void launch_sort(long long M, int key_bits, uint32_t* key_a, uint32_t* idx_a,
+                 uint32_t* key_b, uint32_t* idx_b, int* hist, cudaStream_t s);
+void launch_tile_ranges(int ntiles, long long M, const uint32_t* sorted_keys,
+                        int* tile_begin, int* tile_end, cudaStream_t s);
+
+enum GatherMode {
+  GM_COUPLE = 0,      // force coupling / EBF / modified EBF half step
+  GM_IBM_PREDICT = 1, // aux = wrap(pos + s u(pos))
+  GM_IBM_HALF = 2,    // pos = wrap(pos + s u(aux)); record at aux, F = +F_int
+  GM_IBM_FINAL = 3,   // pos = wrap(pos + s u(aux))
+  GM_IBM1 = 4,        // record at pos, F = +F_int (no gather)
+  GM_ADVECT = 5,      // pos = wrap(pos + s u(pos))
+};
+
+struct GatherArgs {
+  int mode;
+  int kind;             // 2 fc, 3 ebf, 4 mebf
+  int order;            // 1 explicit drag, 2 Crank-Nicolson
+  int include_int;      // F_int enters the coupling force and the kick
+  double s;             // step of this force / position update
+  double gamma, rho0;
+  double rec_weight;    // spread force = rec_weight * (-F^h) (or +F_int)
+  // fluid velocity (j + c1 F1 + c2 F2 + cg g) / rho at the stencil nodes
+  const void* pops; int storage; float scale16;
+  double bb_bot[Q]; double bb_top[Q];
+  const float* F1; const uint8_t* flag1; double c1;
+  const float* F2; const uint8_t* flag2; double c2;
+  double cg; double gvec[3]; double rho0_pop;
+  // particles
+  const uint32_t* perm;           // sorted order (null: identity)
+  double* pos; double* aux; double* vel; const double* fint;
+  const double* mass; double* fh_out;
+  StencilRec* rec;
+};
+void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
+
+struct SpreadArgs {
+  const StencilRec* rec;
+  const int* tile_begin; const int* tile_end;
+  const float* Fin; const uint8_t* flag_in;   // accumulate onto (may be null)
+  float* Fout; uint8_t* flag_out;
+};
+void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s);
+
+// particle momentum sum m v (FP64), one block
+void launch_particle_momentum(long long M, const double* vel, const double* mass,
+                              double* out3, cudaStream_t s);
+
+}  // namespace lbc

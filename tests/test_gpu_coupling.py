@@ -1,0 +1,178 @@
+"""GPU parity of the coupled step (all coupling kinds, orders, splittings and
+stencils) against the FP64 oracle, plus invariants and determinism.
+
+The interpolation and spreading arithmetic of the GPU path is FP32 for every
+population storage (weights, node velocities and the spread force field), the
+particle state and coupling update FP64.  A node velocity of order 1e-2 then
+carries an error of about 1e-9; over the handful of steps run here particle
+velocities, positions and forces agree to 1e-7 absolute, fluid velocities to
+1e-6 relative L2.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import coupling as OC
+from tests.gpu_helpers import make_pair, rel_l2, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _particles(shape, kind, seed, nchains=2, beads=5):
+    nz, ny, nx = shape
+    pos, bonds = synth.bead_chains(nchains, beads, (nx, ny, nz), 1.0, seed=seed)
+    if kind == "ibm":
+        return dict(pos=pos, bonds=bonds, bond_k=0.02, bond_r0=1.3)
+    rng = np.random.default_rng(seed)
+    M = len(pos)
+    return dict(pos=pos, vel=0.01 * rng.standard_normal((M, 3)),
+                mass=rng.uniform(0.5, 2.0, M), bonds=bonds, bond_k=0.3, bond_r0=1.0,
+                ext=1e-4 * rng.standard_normal((M, 3)))
+
+
+SCHEMES = [
+    # kind, order, split, n, stencil
+    ("fc", 2, "base", 1, "trilinear"),
+    ("fc", 2, "base", 1, "peskin4"),
+    ("fc", 2, "base", 1, "peskin3"),
+    ("fc", 2, "inside", 2, "trilinear"),
+    ("fc", 2, "outside", 2, "trilinear"),
+    ("fc", 2, "outside", 1, "peskin4"),
+    ("ebf", 2, "base", 1, "peskin4"),
+    ("mebf", 2, "base", 1, "peskin4"),
+    ("mebf", 2, "inside", 1, "trilinear"),
+    ("fc", 1, "base", 1, "trilinear"),
+    ("mebf", 1, "base", 1, "peskin3"),
+    ("ibm", 2, "base", 1, "peskin4"),
+    ("ibm", 2, "base", 1, "trilinear"),
+    ("ibm", 1, "base", 1, "peskin4"),
+]
+
+
+@pytest.mark.parametrize("kind,order,split,n,stencil", SCHEMES)
+@pytest.mark.parametrize("walls", [False, True])
+def test_coupled_steps_match_oracle(kind, order, split, n, stencil, walls):
+    require_cuda()
+    shape = (11, 10, 12)
+    fbar0 = synth.random_populations(shape, seed=21, amp=1e-3)
+    parts = _particles(shape, kind, seed=5)
+    if walls:       # keep markers clear of the walls
+        parts["pos"][:, 2] = 3.0 + np.mod(parts["pos"][:, 2], shape[0] - 6.0)
+    uw = ((0.01, 0, 0), (-0.01, 0.005, 0)) if walls else ((0, 0, 0), (0, 0, 0))
+    box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=(1e-5, 0, -1e-5),
+                        walls=walls, uw=uw, storage="f64", kind=kind, order=order,
+                        stencil=stencil, gamma=1.7, split=split, n=n, parts=parts)
+    for nsteps in (1, 2, 3):
+        box.step(nsteps)
+        for _ in range(nsteps):
+            sm.step()
+        pos, vel, fh = box.get_particles()
+        d = OC.min_image(pos - sm.parts.pos, shape, walls)
+        assert np.abs(d).max() < 1e-7, np.abs(d).max()
+        if kind != "ibm":
+            assert np.abs(vel - sm.parts.vel).max() < 1e-7
+            assert np.abs(fh - sm.last_Fh).max() < 1e-7
+    _, u = box.get_fields()
+    assert rel_l2(u, sm.fluid_velocity()) < 1e-6
+    box.close()
+
+
+@pytest.mark.parametrize("kind,order,split,n", [("fc", 2, "base", 1), ("fc", 2, "outside", 2),
+                                                ("mebf", 2, "inside", 2), ("ibm", 2, "base", 1),
+                                                ("fc", 1, "base", 1)])
+def test_total_momentum_budget_on_gpu(kind, order, split, n):
+    """Periodic box: fluid + particle momentum grows by exactly h g N per
+    step (Sec. 5.2: the coupling conserves total momentum)."""
+    require_cuda()
+    shape = (12, 12, 12)
+    fbar0 = synth.random_populations(shape, seed=3)
+    parts = _particles(shape, kind, seed=8, nchains=4, beads=6)
+    g = np.array([1e-5, -2e-5, 0.0])
+    box, _ = make_pair(shape, fbar0, coll="bgk", tau=0.9, g=g, storage="f64", kind=kind,
+                       order=order, stencil="peskin4", gamma=2.0, split=split, n=n,
+                       parts=parts)
+    m0, P0, _ = box.invariants()
+    N = np.prod(shape)
+    for t in (1, 3, 6):
+        box.step(t if t == 1 else 2 if t == 3 else 3)
+        m, P, st = box.invariants()
+        assert st == 0
+        assert abs(m - m0) < 1e-9
+        assert np.abs(P - P0 - t * g * N).max() < 1e-8, (t, P - P0 - t * g * N)
+    box.close()
+
+
+def test_spreading_is_deterministic():
+    """Same inputs, fresh boxes: bit-identical particles and fluid (no
+    atomics: the summation order of the spreading is fixed)."""
+    require_cuda()
+    shape = (16, 16, 16)
+    fbar0 = synth.random_populations(shape, seed=1)
+    parts = _particles(shape, "fc", seed=2, nchains=6, beads=10)
+    outs = []
+    for _ in range(2):
+        box, _ = make_pair(shape, fbar0, coll="mrt", tau=0.8, storage="f32", kind="fc",
+                           stencil="peskin4", gamma=3.0, parts=parts)
+        box.step(6)
+        outs.append((box.get_populations(), box.get_particles()))
+        box.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in range(3):
+        assert np.array_equal(outs[0][1][k], outs[1][1][k])
+
+
+def test_cfg1_point_particle_32_fp64():
+    """32^3 FP64 BGK tau = 0.8, one particle with force coupling gamma = m = 1,
+    trilinear, v0 = (0.01, 0, 0): second- and first-order schemes against the
+    oracle, and conservation of m v0 in the periodic box."""
+    require_cuda()
+    c = synth.config("cfg1_fc_point_32")
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    from oracle import lattice as OLat
+    fbar0 = OLat.equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    parts = dict(pos=np.array([c["particle"]]), vel=np.array([c["velocity"]]), mass=1.0)
+    for order, steps in ((2, 300), (1, 100)):
+        box, sm = make_pair(shape, fbar0, coll="bgk", tau=c["tau"], storage="f64",
+                            kind="fc", order=order, stencil="trilinear",
+                            gamma=c["gamma"], parts=parts)
+        for chunk in (1, steps // 2 - 1, steps - steps // 2):
+            box.step(chunk)
+            for _ in range(chunk):
+                sm.step()
+            pos, vel, _ = box.get_particles()
+            assert np.abs(vel - sm.parts.vel).max() < 1e-9
+            assert np.abs(pos - sm.parts.pos).max() < 1e-8
+        m, P, _ = box.invariants()
+        assert np.abs(P - np.array(c["velocity"])).max() < 1e-12
+        box.close()
+
+
+def test_cfg2_reduced_mrt_chains():
+    """The 256^3 chain workload at 1/4 size: 64^3 MRT FP32, bead chains with
+    k = 10 bonds, force coupling gamma = 5, body force 1e-6, the Sec. 6 split
+    with two particle sub-steps per half step."""
+    require_cuda()
+    c = synth.config("cfg2_mrt_chains_256", scale=4)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    pos, bonds = synth.bead_chains(c["nchains"], c["beads"], c["box"], c["bond_r0"],
+                                   seed=c["seed"])
+    parts = dict(pos=pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
+                 bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+    from oracle import lattice as OLat
+    fbar0 = OLat.equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    box, sm = make_pair(shape, fbar0, coll="mrt", tau=c["tau"], g=c["body_force"],
+                        storage="f32", kind="fc", stencil="trilinear", gamma=c["gamma"],
+                        split=c["mode"], n=c["substeps"], parts=parts)
+    steps = 12
+    box.step(steps)
+    for _ in range(steps):
+        sm.step()
+    pos_g, vel_g, fh_g = box.get_particles()
+    d = OC.min_image(pos_g - sm.parts.pos, shape, False)
+    assert np.abs(d).max() < 1e-6
+    assert rel_l2(vel_g, sm.parts.vel) < 1e-5
+    _, u = box.get_fields()
+    assert rel_l2(u, sm.fluid_velocity()) < 1e-5
+    box.close()
