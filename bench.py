@@ -1,0 +1,380 @@
+"""Benchmark of the coupled D3Q19 step on the 256^3 bead-chain workload.
+
+Workload (the single-box configuration the throughput metric is quoted on):
+256^3 periodic box, MRT collision (shear rate 1/tau, tau = 1), FP32
+populations stored as deviations from w_i rho0, 2000 bead chains of 50 beads
+(100 000 particles, harmonic bonds k = 10, r0 = 1), viscous force coupling
+gamma = 5, m = 1, trilinear interpolation and spreading, body force 1e-6
+along x, the multiple-time-step split of Sec. 6 (Eq. [multistep]) with two
+coupled particle sub-steps per half step.  Inputs are synthetic and seeded
+(synth/).
+
+One "step" is one full coupled time step (drift/forces, marker binning,
+interpolation + coupling, spreading, fused LB step).  value = million lattice
+updates per second (MLUPS) of the whole job over all ranks; the population
+arrays (1.27 GB each) are larger than L2, so no flush is needed.
+
+Printed as one JSON line (rank 0).  --impl reference times the FP64 oracle
+on the host cores instead (a bounded sample of the same workload).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled D3Q19 MLUPS & % of HBM peak; ensemble jobs/s with p50/p99 latency"
+WORKLOAD = "cfg2_mrt_chains_256"
+LB_KERNEL_SOURCES = ["paper_1406_2211_gb300/csrc/lb_kernels.cu",
+                     "paper_1406_2211_gb300/csrc/lb_device.cuh",
+                     "paper_1406_2211_gb300/csrc/lbc_common.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "lb_step_mrt_f32_256.md")
+
+
+def lb_source_hash():
+    h = hashlib.sha256()
+    for f in LB_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per LB launch from the committed ncu summary, if it was
+    taken on the current LB kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_hash = re.search(r"lb_source_hash:\s*([0-9a-f]+)", text)
+    m_traf = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_traf or m_hash.group(1) != lb_source_hash():
+        return None
+    return float(m_traf.group(1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+def workload(scale=1):
+    import synth
+    c = synth.config(WORKLOAD, scale=scale)
+    pos, bonds = synth.bead_chains(c["nchains"], c["beads"], c["box"], c["bond_r0"],
+                                   seed=c["seed"])
+    return c, pos, bonds
+
+
+def make_box(c, npart, nbonds):
+    from paper_1406_2211_gb300 import lbc
+    nx, ny, nz = c["box"]
+    lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"],
+                           rho0=c["rho0"], body_force=c["body_force"], storage=c["storage"])
+    cpl = lbc.coupling_desc(c["kind"], 2, c["stencil"], gamma=c["gamma"], split=c["mode"],
+                            substeps=c["substeps"])
+    return lbc.Box(lat, cpl, max_particles=npart, max_bonds=nbonds)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "lbc_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    c, pos, bonds = workload()
+    nx, ny, nz = c["box"]
+    cells = nx * ny * nz
+    M, B = len(pos), len(bonds)
+    stream = torch.cuda.current_stream()
+
+    box = make_box(c, M, B)
+    box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+    box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
+                      bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+    box.step(args.warmup)
+    from paper_1406_2211_gb300 import lbc
+    box.set_option(lbc.LBC_OPT_TIMING, args.steps + 4)
+    # the graphs are recaptured with timing nodes: one eager step + one
+    # replay before the timed region keeps capture out of it
+    box.step(3)
+    box.lb_timing(reset=True)
+    launches_per_step = box.launches_per_step()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    lb_ms, lb_n = box.lb_timing(reset=True)
+    m_end, P_end, st = box.invariants()
+    if st != 0:
+        raise RuntimeError("non-finite state after the timed steps")
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (fused LB step): algorithmic bytes =
+    # 2 x 19 populations x 4 bytes per cell
+    pop_bytes = box.population_bytes()
+    alg_bytes = 2 * 19 * 4 * cells
+    lb_avg_ms = lb_ms / max(lb_n, 1)
+    achieved = alg_bytes / (lb_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI with host buffers: upload particles,
+    # step, read particles and invariants back (copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        box.close()
+        del box
+        torch.cuda.empty_cache()
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hpos, hvel = pin(pos), pin(np.zeros_like(pos))
+        box2 = make_box(c, M, B)
+        box2.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        box2.set_particles(hpos, vel=hvel, mass=c["mass"], bonds=bonds,
+                           bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+        box2.step(args.steps)
+        rpos, rvel, _ = box2.get_particles()
+        _, _, st2 = box2.invariants()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+        h2d = hpos.nbytes + hvel.nbytes + M * 8 + bonds.nbytes + 2 * B * 8
+        d2h = rpos.nbytes + rvel.nbytes + M * 24 + 4 * 8
+        e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "scope": "lbc_box_set_particles (host arrays) + lbc_box_step + "
+                        "lbc_box_get_particles + lbc_box_invariants"}
+        box2.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded bead chains, fluid at rest)",
+        "config": {"workload": WORKLOAD, "box": [nx, ny, nz], "collision": "mrt",
+                   "tau": c["tau"], "storage": "f32 deviations", "particles": M,
+                   "bonds": B, "coupling": "force coupling, gamma=5, m=1",
+                   "stencil": "trilinear", "split": "Eq. multistep, n=2 coupled sub-steps per half",
+                   "body_force": list(c["body_force"]),
+                   "l2": "inputs larger than L2 (2 x %.2f GB population arrays)" % (pop_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "lb_step_kernel (fused LB step)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": lb_avg_ms,
+                     "launches_timed": lb_n,
+                     "lb_share_of_step": lb_ms / ms if ms > 0 else None},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    return line
+
+
+# ------------------------------------------------------------------ CPU arm
+def oracle_sample(max_seconds, min_steps=2, max_steps=None):
+    """The FP64 oracle on a bounded sample of the workload: the 256^3 box cut
+    to 64^3 with 1/64 of the chains (same density), MRT, same coupling.
+    Runs in this process with one BLAS thread.  Returns (MLUPS, steps, s)."""
+    import numpy as np
+    from oracle import coupling as OC
+    from oracle import lattice as OLat
+    from oracle import lb as OL
+    from oracle import sim as OS
+    c, pos, bonds = workload(scale=4)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    p = OL.LBParams(collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                    body_force=c["body_force"])
+    parts = OC.Particles(pos, vel=np.zeros_like(pos), mass=np.full(len(pos), c["mass"]),
+                         bonds=bonds, bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+    sm = OS.Sim(shape, p, OS.CouplingParams("fc", 2, c["stencil"], gamma=c["gamma"],
+                                            substeps=c["substeps"], mode=c["mode"]),
+                parts, fbar=OLat.equilibrium(np.full(shape, c["rho0"]),
+                                             np.zeros((3,) + shape)))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        sm.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if max_steps is not None and n >= max_steps:
+            break
+        if n >= min_steps and el >= max_seconds:
+            break
+    cells = nx * ny * nz
+    return cells * n / el / 1e6, n, el, "%dx%dx%d box, %d particles, %d steps" % (
+        nx, ny, nz, len(pos), n)
+
+
+def cpu_baseline_subprocess(max_seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%f)))" % (ROOT, max_seconds))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    v, n, el, sample = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 NumPy oracle, " + sample + " (%.1f s)" % el}
+
+
+def run_reference(args):
+    """--impl reference: the oracle, timed on the host cores, K steps of a
+    bounded sample of the workload (rank 0 only)."""
+    env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"}
+    for k, v in env_threads.items():
+        os.environ.setdefault(k, v)
+    # warm-up and timed steps on the 64^3 sample; each step ~0.3 s
+    oracle_sample(0.0, min_steps=args.warmup, max_steps=args.warmup)
+    steps = min(args.steps, 60)
+    v, n, el, sample = oracle_sample(0.0, min_steps=steps, max_steps=steps)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS",
+            "n_gpus": 0, "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded bead chains, fluid at rest)",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "FP64 NumPy oracle, " + sample +
+                                       " (steps capped at 60 of the requested %d)" % args.steps},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the oracle process is started before any CUDA work
+        cpu = cpu_baseline_subprocess(args.cpu_seconds)
+    line = run_gpu(args, rank, world, local_rank)
+    line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

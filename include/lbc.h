@@ -206,9 +206,22 @@ lbc_status lbc_box_invariants(lbc_box* box, double* mass, double* momentum,
 /* Latched device status of the box (LBC_OK or the first error seen). */
 lbc_status lbc_box_status(const lbc_box* box);
 
-/* Options: LBC_OPT_GRAPHS (1 = capture steps in CUDA graphs, default 1). */
+/* Options:
+ *  LBC_OPT_GRAPHS  1 = replay steps as captured CUDA graphs (default), 0 =
+ *                  launch every kernel eagerly.
+ *  LBC_OPT_TIMING  n > 0: bracket each of the next n launches of the fused
+ *                  LB kernel with a pair of CUDA events recorded on the
+ *                  launching stream (inside the graphs as event-record
+ *                  nodes); 0 = off.  Read with lbc_box_lb_timing(). */
 #define LBC_OPT_GRAPHS 1
+#define LBC_OPT_TIMING 2
 lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
+
+/* Sum of the event-measured durations (ms) of the LB kernel launches timed
+ * since the last reset, and their count; waits for the last event.
+ * reset != 0 restarts the count. */
+lbc_status lbc_box_lb_timing(lbc_box* box, double* ms_total, int64_t* launches,
+                             int32_t reset);
 
 /* Number of kernel launches one time step enqueues for this box (for
  * launch accounting). */

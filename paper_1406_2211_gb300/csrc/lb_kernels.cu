@@ -27,22 +27,55 @@
 
 namespace lbc {
 
-// E_i(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 u.u   (f_i^eq = w_i rho (1 + E_i(u)))
+// Equilibrium in a form without shared inexact constants.  With w_i = n_i/36
+// (n_i = 12, 2, 1) the deviation of f_i^eq from w_i rho0 is
+//   w_i (rho - rho0) + w_i rho E_i(u)
+//     = n_i [ (rho - rho0)/36 + c_i.(rho u)/12 + rho ((c_i.u)^2/8 - u.u/24) ].
+// Dividing the moments by 36 and 12 (correctly rounded, so errors are
+// unbiased) instead of multiplying every population by a rounded w_i keeps
+// FP32 from adding a systematic (1 + eps) factor to the momentum at every
+// collision (with w_i in FP32 the shear-wave amplitude drifted by 1e-8 per
+// step).
+__host__ __device__ constexpr int n_of(int i) { return i == 0 ? 12 : (i <= 6 ? 2 : 1); }
+
+// x / D to within one rounding, without a division: x * hi + x * lo where
+// hi + lo represents 1/D to twice the working precision, so the result
+// carries no bias from a rounded reciprocal
+template <typename C, int D>
+__device__ inline C div_by(C x) {
+  constexpr double inv = 1.0 / D;
+  constexpr C hi = C(inv);
+  constexpr C lo = C(inv - double(hi));
+  return fma(x, hi, x * lo);
+}
+
+// Q_i(u) = (c_i.u)^2/8 - u.u/24, with uu24 = u.u/24 precomputed
 template <typename C, int I>
-__device__ inline C eq_poly(C ux, C uy, C uz, C uu) {
+__device__ inline C quad_part(C ux, C uy, C uz, C uu24) {
   constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
   C cu = C(0);
   if (cx) cu += C(cx) * ux;
   if (cy) cu += C(cy) * uy;
   if (cz) cu += C(cz) * uz;
-  return cu * (C(3) + C(4.5) * cu) - C(1.5) * uu;
+  return cu * cu * C(0.125) - uu24;
 }
 
-template <typename C, int I = 0>
-__device__ inline void eq_all(C ux, C uy, C uz, C (&e)[Q]) {
+template <typename C, int I>
+__device__ inline C lin_part(C qx, C qy, C qz) {
+  constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+  C cq = C(0);
+  if (cx) cq += C(cx) * qx;
+  if (cy) cq += C(cy) * qy;
+  if (cz) cq += C(cz) * qz;
+  return cq;
+}
+
+template <int I> struct IC { static constexpr int value = I; };
+template <int I = 0, typename F>
+__device__ inline void unroll_q(F&& f) {
   if constexpr (I < Q) {
-    e[I] = eq_poly<C, I>(ux, uy, uz, ux * ux + uy * uy + uz * uz);
-    eq_all<C, I + 1>(ux, uy, uz, e);
+    f(IC<I>{});
+    unroll_q<I + 1>(f);
   }
 }
 
@@ -120,46 +153,64 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   C Fx = C(a.cg * a.gvec[0]), Fy = C(a.cg * a.gvec[1]), Fz = C(a.cg * a.gvec[2]);
   if (FORCED) {
     const int t = tile_of(g, x, y, z);
-    if (a.Fa && a.flag_a[t]) {
-      Fx += C(a.ca) * C(a.Fa[cell]);
-      Fy += C(a.ca) * C(a.Fa[g.qstride + cell]);
-      Fz += C(a.ca) * C(a.Fa[2 * g.qstride + cell]);
+    const C* Fa = static_cast<const C*>(a.Fa);
+    const C* Fb = static_cast<const C*>(a.Fb);
+    if (Fa && a.flag_a[t]) {
+      Fx += C(a.ca) * Fa[cell];
+      Fy += C(a.ca) * Fa[g.qstride + cell];
+      Fz += C(a.ca) * Fa[2 * g.qstride + cell];
     }
-    if (a.Fb && a.flag_b[t]) {
-      Fx += C(a.cb) * C(a.Fb[cell]);
-      Fy += C(a.cb) * C(a.Fb[g.qstride + cell]);
-      Fz += C(a.cb) * C(a.Fb[2 * g.qstride + cell]);
+    if (Fb && a.flag_b[t]) {
+      Fx += C(a.cb) * Fb[cell];
+      Fy += C(a.cb) * Fb[g.qstride + cell];
+      Fz += C(a.cb) * Fb[2 * g.qstride + cell];
     }
   }
   const C u1x = u0x + Fx * inv, u1y = u0y + Fy * inv, u1z = u0z + Fz * inv;
 
-  C e0[Q], e1[Q];
-  eq_all<C>(u0x, u0y, u0z, e0);
-  eq_all<C>(u1x, u1y, u1z, e1);
+  const C uu0 = div_by<C, 24>(u0x * u0x + u0y * u0y + u0z * u0z);
+  const C uu1 = div_by<C, 24>(u1x * u1x + u1y * u1y + u1z * u1z);
 
   if (COLL == 0) {
+    // f*_i = gamma fbar_i + n_i [ (1-gamma) rd/36 + c_i.((1-gamma) j + F)/12
+    //                             + rho (Q_i(u1) - gamma Q_i(u0)) ]
     const C gam = C(a.gamma_bgk);
     const C omg = C(1) - gam;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const C wi = C(w_of(i));
-      const C v = gam * f[i] + wi * (omg * rd + rho * (e1[i] - gam * e0[i]));
+    const C sm = div_by<C, 36>(omg * rd);
+    const C qx = div_by<C, 12>(omg * jx + Fx), qy = div_by<C, 12>(omg * jy + Fy),
+            qz = div_by<C, 12>(omg * jz + Fz);
+    auto body = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const C q0 = quad_part<C, i>(u0x, u0y, u0z, uu0);
+      const C q1 = quad_part<C, i>(u1x, u1y, u1z, uu1);
+      const C v = gam * f[i] + C(n_of(i)) * (sm + lin_part<C, i>(qx, qy, qz) + rho * (q1 - gam * q0));
       Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
-    }
+    };
+    unroll_q(body);
   } else {
+    // neq_i = fbar_i - f_i^eq(rho, u0); relax per moment; add f^eq(rho, u1)
+    const C md = div_by<C, 36>(rd);
+    const C j0x = div_by<C, 12>(jx), j0y = div_by<C, 12>(jy), j0z = div_by<C, 12>(jz);
+    const C j1x = div_by<C, 12>(jx + Fx), j1y = div_by<C, 12>(jy + Fy), j1z = div_by<C, 12>(jz + Fz);
     C neq[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) neq[i] = f[i] - C(w_of(i)) * (rd + rho * e0[i]);
+    auto fill = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      neq[i] = f[i] - C(n_of(i)) * (md + lin_part<C, i>(j0x, j0y, j0z) +
+                                    rho * quad_part<C, i>(u0x, u0y, u0z, uu0));
+    };
+    unroll_q(fill);
     const C gk[5] = {C(0), C(a.gamma_k[0]), C(a.gamma_k[1]), C(a.gamma_k[2]), C(a.gamma_k[3])};
     C m[Q];
     moments_all<C>(neq, gk, m);
     C post[Q];
     back_all<C>(m, post);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const C v = C(w_of(i)) * (rd + rho * e1[i]) + post[i];
+    auto out = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
+                                rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + post[i];
       Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
-    }
+    };
+    unroll_q(out);
   }
 }
 
@@ -266,10 +317,11 @@ __global__ void fields_kernel(const S* __restrict__ fstar, const LBArgs a, doubl
   }
   const double rho = a.rho0 + rd;
   const int t = tile_of(g, x, y, z);
-  const bool fa = a.Fa != nullptr && a.flag_a[t];
+  const C* Fa = static_cast<const C*>(a.Fa);
+  const bool fa = Fa != nullptr && a.flag_a[t];
   for (int c = 0; c < 3; ++c) {
     double jj = j[c] + cg * a.gvec[c];
-    if (fa) jj += ca * double(a.Fa[c * g.qstride + cell]);
+    if (fa) jj += ca * double(Fa[c * g.qstride + cell]);
     u_out[c * N + dense] = jj / rho;
   }
   rho_out[dense] = rho;
@@ -306,10 +358,11 @@ invariants_kernel(const S* __restrict__ fstar, const LBArgs a, double ca, double
       }
       const long long cell = z * g.plane + (long long)y * g.pitch + x;
       const int t = tile_of(g, x, y, z);
-      if (a.Fa != nullptr && a.flag_a[t]) {
-        j0 += ca * double(a.Fa[cell]);
-        j1 += ca * double(a.Fa[g.qstride + cell]);
-        j2 += ca * double(a.Fa[2 * g.qstride + cell]);
+      const C* Fa = static_cast<const C*>(a.Fa);
+      if (Fa != nullptr && a.flag_a[t]) {
+        j0 += ca * double(Fa[cell]);
+        j1 += ca * double(Fa[g.qstride + cell]);
+        j2 += ca * double(Fa[2 * g.qstride + cell]);
       }
       j0 += cg * a.gvec[0]; j1 += cg * a.gvec[1]; j2 += cg * a.gvec[2];
       acc[0] += rd; acc[1] += j0; acc[2] += j1; acc[3] += j2;

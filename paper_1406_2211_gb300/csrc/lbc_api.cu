@@ -87,7 +87,7 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
   L.pop_bytes = (size_t)Q * (size_t)g.qstride * L.esize;
   L.off_pop[0] = take(L.pop_bytes);
   L.off_pop[1] = take(L.pop_bytes);
-  const size_t fbytes = 3 * (size_t)g.qstride * sizeof(float);
+  const size_t fbytes = 3 * (size_t)g.qstride * force_elem_bytes(l->storage);
   if (L.has_particles) {
     L.off_F[0] = take(fbytes); L.off_F[1] = take(fbytes);
     L.off_flag[0] = take(L.ntiles); L.off_flag[1] = take(L.ntiles);
@@ -104,7 +104,7 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_hist = take(sort_scratch_ints(M) * sizeof(int));
     L.off_tb = take((size_t)L.ntiles * 4);
     L.off_te = take((size_t)L.ntiles * 4);
-    L.off_rec = take((size_t)M * sizeof(StencilRec));
+    L.off_rec = take((size_t)M * stencil_rec_bytes(l->storage));
     L.off_nbr_start = take((size_t)(M + 1) * 4);
     const size_t nb2 = (size_t)(2 * B > 0 ? 2 * B : 1);
     L.off_nbr_j = take(nb2 * 4);
@@ -132,13 +132,22 @@ struct lbc_box {
   bool steady;      // at least one step done (graphs capture steady state)
   int use_graphs;
   cudaGraphExec_t graph[2];   // two-step graphs, by starting parity of cur
+  cudaGraph_t tgraph[2];      // their templates (node handles for updates)
   cudaStream_t graph_stream[2];
+  // LB-kernel timing: event pairs around every LB launch (see LBC_OPT_TIMING)
+  int64_t timing_cap;         // pairs available (0 = off)
+  int64_t timing_used;        // pairs recorded since the last reset
+  std::vector<cudaEvent_t> tev;   // 2 * timing_cap events + 4 spare
+  cudaEvent_t ph[4];          // placeholders recorded while capturing
+  cudaGraphNode_t tnode[2][4];    // event-record nodes of each graph
+  bool capturing;
+  int lb_in_capture;
   lbc_status status;
   LBArgs lb;        // constant part of the LB arguments
   int64_t launches;
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
-  float* F(int k) { return L.has_particles ? reinterpret_cast<float*>(arena + L.off_F[k]) : nullptr; }
+  void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
   uint8_t* flag(int k) { return L.has_particles ? reinterpret_cast<uint8_t*>(arena + L.off_flag[k]) : nullptr; }
   double* dptr(size_t off) { return reinterpret_cast<double*>(arena + off); }
   uint32_t* uptr(size_t off) { return reinterpret_cast<uint32_t*>(arena + off); }
@@ -203,6 +212,7 @@ PartArgs part_args(lbc_box* b) {
   p.M = b->M;
   p.stencil = b->cpl.stencil;
   p.S = p.stencil == 0 ? 2 : (p.stencil == 1 ? 4 : 3);
+  p.storage = b->lat.storage;
   return p;
 }
 
@@ -212,12 +222,25 @@ struct Plan {
   cudaStream_t s;
   int64_t n = 0;   // launches enqueued
 
-  void lb(const float* Fa, const float* Fb, double ca, double cb, double cg) {
+  void lb(const void* Fa, const void* Fb, double ca, double cb, double cg) {
     LBArgs a = b->lb;
     a.Fa = Fa; a.flag_a = Fa ? (Fa == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.Fb = Fb; a.flag_b = Fb ? (Fb == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.ca = ca; a.cb = cb; a.cg = cg;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->timing_cap > 0) {
+      if (b->capturing) {
+        const int k = b->lb_in_capture++;
+        if (k < 2) { e0 = b->ph[2 * k]; e1 = b->ph[2 * k + 1]; }
+      } else if (b->timing_used < b->timing_cap) {
+        e0 = b->tev[2 * b->timing_used];
+        e1 = b->tev[2 * b->timing_used + 1];
+        ++b->timing_used;
+      }
+    }
+    if (e0) cudaEventRecord(e0, s);
     launch_lb_step(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
+    if (e1) cudaEventRecord(e1, s);
     b->cur = 1 - b->cur;
     ++n;
   }
@@ -283,7 +306,7 @@ struct Plan {
     a.fint = b->dptr(b->L.off_fint);
     a.mass = b->dptr(b->L.off_mass);
     a.fh_out = b->dptr(b->L.off_fh);
-    a.rec = reinterpret_cast<StencilRec*>(b->arena + b->L.off_rec);
+    a.rec = b->arena + b->L.off_rec;
     return a;
   }
 
@@ -300,7 +323,7 @@ struct Plan {
 
   void spread(int out, bool carry) {
     SpreadArgs a{};
-    a.rec = reinterpret_cast<const StencilRec*>(b->arena + b->L.off_rec);
+    a.rec = b->arena + b->L.off_rec;
     a.tile_begin = b->iptr(b->L.off_tb);
     a.tile_end = b->iptr(b->L.off_te);
     a.Fin = carry ? b->F(out) : nullptr;
@@ -478,8 +501,11 @@ lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
     const int cur0 = b->cur, ia0 = b->ia, pc0 = b->pc;
     const bool sorted0 = b->sorted;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    b->capturing = true;
+    b->lb_in_capture = 0;
     enqueue_step(b, cs, &dummy);
     enqueue_step(b, cs, &dummy);
+    b->capturing = false;
     cudaGraph_t graph;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (own) cudaStreamDestroy(cs);
@@ -490,12 +516,41 @@ lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
     }
     cudaGraphExec_t exec;
     e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return LBC_ERR_CUDA;
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return LBC_ERR_CUDA;
+    }
+    for (int k = 0; k < 4; ++k) b->tnode[par][k] = nullptr;
+    if (b->timing_cap > 0) {
+      size_t nn = 0;
+      CK(cudaGraphGetNodes(graph, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int k = 0; k < 4; ++k)
+          if (ev == b->ph[k]) b->tnode[par][k] = nd;
+      }
+    }
     b->graph[par] = exec;
+    b->tgraph[par] = graph;
     b->graph_stream[par] = s;
   }
   while (nsteps >= 2) {
+    if (b->timing_cap > 0 && b->tnode[par][0]) {
+      // point the four event-record nodes at fresh pool events (or at the
+      // spare ones once the pool is used up)
+      const bool room = b->timing_used + 2 <= b->timing_cap;
+      for (int k = 0; k < 4; ++k) {
+        cudaEvent_t ev = room ? b->tev[2 * b->timing_used + k] : b->tev[2 * b->timing_cap + k];
+        CK(cudaGraphExecEventRecordNodeSetEvent(b->graph[par], b->tnode[par][k], ev));
+      }
+      if (room) b->timing_used += 2;
+    }
     CK(cudaGraphLaunch(b->graph[par], s));
     nsteps -= 2;
   }
@@ -509,10 +564,23 @@ lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
 void reset_graphs(lbc_box* b) {
   for (int k = 0; k < 2; ++k) {
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    if (b->tgraph[k]) cudaGraphDestroy(b->tgraph[k]);
     b->graph[k] = nullptr;
+    b->tgraph[k] = nullptr;
     b->graph_stream[k] = nullptr;
   }
   b->steady = false;
+}
+
+void free_timing(lbc_box* b) {
+  for (cudaEvent_t e : b->tev) cudaEventDestroy(e);
+  b->tev.clear();
+  for (int k = 0; k < 4; ++k) {
+    if (b->ph[k]) cudaEventDestroy(b->ph[k]);
+    b->ph[k] = nullptr;
+  }
+  b->timing_cap = 0;
+  b->timing_used = 0;
 }
 
 lbc_status clear_pending(lbc_box* b, cudaStream_t s) {
@@ -647,7 +715,13 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->sorted = false; b->steady = false;
   b->use_graphs = 1;
   b->graph[0] = b->graph[1] = nullptr;
+  b->tgraph[0] = b->tgraph[1] = nullptr;
   b->graph_stream[0] = b->graph_stream[1] = nullptr;
+  b->timing_cap = 0;
+  b->timing_used = 0;
+  for (int k = 0; k < 4; ++k) b->ph[k] = nullptr;
+  b->capturing = false;
+  b->lb_in_capture = 0;
   b->status = LBC_OK;
   b->launches = 0;
   fill_lb_args(b);
@@ -668,6 +742,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
 lbc_status lbc_box_destroy(lbc_box* b) {
   if (!b) return LBC_ERR_ARG;
   reset_graphs(b);
+  free_timing(b);
   delete b;
   return LBC_OK;
 }
@@ -739,14 +814,21 @@ lbc_status lbc_box_set_pending_force(lbc_box* b, const double* Fa, void* stream)
   if (!Fa) return clear_pending(b, s);
   const Geom& g = b->L.g;
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  std::vector<float> host(3 * (size_t)g.qstride, 0.0f);
+  const bool dbl = b->lat.storage == LBC_F64;
+  std::vector<double> hd(dbl ? 3 * (size_t)g.qstride : 0, 0.0);
+  std::vector<float> hf(dbl ? 0 : 3 * (size_t)g.qstride, 0.0f);
   for (int c = 0; c < 3; ++c)
     for (int z = 0; z < g.nz; ++z)
       for (int y = 0; y < g.ny; ++y)
-        for (int x = 0; x < g.nx; ++x)
-          host[(size_t)c * g.qstride + (size_t)z * g.plane + (size_t)y * g.pitch + x] =
-              (float)Fa[(size_t)c * N + ((size_t)z * g.ny + y) * g.nx + x];
-  CK(cudaMemcpyAsync(b->F(b->ia), host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        for (int x = 0; x < g.nx; ++x) {
+          const size_t at = (size_t)c * g.qstride + (size_t)z * g.plane + (size_t)y * g.pitch + x;
+          const double v = Fa[(size_t)c * N + ((size_t)z * g.ny + y) * g.nx + x];
+          if (dbl) hd[at] = v; else hf[at] = (float)v;
+        }
+  if (dbl)
+    CK(cudaMemcpyAsync(b->F(b->ia), hd.data(), hd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  else
+    CK(cudaMemcpyAsync(b->F(b->ia), hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->flag(b->ia), 1, b->L.ntiles, s));
   reset_graphs(b);
   CK(cudaStreamSynchronize(s));
@@ -833,7 +915,7 @@ lbc_status lbc_box_get_fields(lbc_box* b, double* rho, double* u, void* stream) 
   double* stage = static_cast<double*>(b->pop(1 - b->cur));
   LBArgs a = b->lb;
   const bool o2 = order2(b);
-  a.Fa = particles(b) && o2 ? b->F(b->ia) : nullptr;
+  a.Fa = b->L.has_particles && o2 ? b->F(b->ia) : nullptr;
   a.flag_a = a.Fa ? b->flag(b->ia) : nullptr;
   launch_fields(b->lat.storage, b->pop(b->cur), a, o2 ? 0.5 : 0.0, o2 ? 0.5 : 0.0, stage, stage + N, s);
   if (rho) CK(cudaMemcpyAsync(rho, stage, N * 8, cudaMemcpyDeviceToHost, s));
@@ -865,7 +947,7 @@ lbc_status lbc_box_invariants(lbc_box* b, double* mass, double* momentum, void* 
   cudaStream_t s = S(stream);
   LBArgs a = b->lb;
   const bool o2 = order2(b);
-  a.Fa = particles(b) && o2 ? b->F(b->ia) : nullptr;
+  a.Fa = b->L.has_particles && o2 ? b->F(b->ia) : nullptr;
   a.flag_a = a.Fa ? b->flag(b->ia) : nullptr;
   double* out = b->dptr(b->L.off_redout);
   launch_invariants(b->lat.storage, b->pop(b->cur), a, o2 ? 0.5 : 0.0, o2 ? 0.5 : 0.0,
@@ -893,7 +975,33 @@ lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
     reset_graphs(b);
     return LBC_OK;
   }
+  if (option == LBC_OPT_TIMING) {
+    if (value < 0) return LBC_ERR_ARG;
+    reset_graphs(b);
+    free_timing(b);
+    if (value == 0) return LBC_OK;
+    b->tev.resize(2 * (size_t)value + 4, nullptr);
+    for (auto& e : b->tev) CK(cudaEventCreate(&e));
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&b->ph[k]));
+    b->timing_cap = value;
+    return LBC_OK;
+  }
   return LBC_ERR_ARG;
+}
+
+lbc_status lbc_box_lb_timing(lbc_box* b, double* ms_total, int64_t* launches, int32_t reset) {
+  if (!b || !ms_total || !launches) return LBC_ERR_ARG;
+  double tot = 0.0;
+  for (int64_t k = 0; k < b->timing_used; ++k) {
+    CK(cudaEventSynchronize(b->tev[2 * k + 1]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, b->tev[2 * k], b->tev[2 * k + 1]));
+    tot += ms;
+  }
+  *ms_total = tot;
+  *launches = b->timing_used;
+  if (reset) b->timing_used = 0;
+  return LBC_OK;
 }
 
 int64_t lbc_box_launches_per_step(const lbc_box* b) {

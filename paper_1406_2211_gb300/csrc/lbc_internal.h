@@ -23,9 +23,11 @@ struct LBArgs {
   double gvec[3];         // uniform body force density g
   double bb_bot[Q];       // moving-wall term of population i arriving from
   double bb_top[Q];       //   the bottom / top wall: 6 w_i rho0 c_i . u_w
-  // sparse force fields (may be null): F[c * qstride + cell], flags per tile
-  const float* Fa; const uint8_t* flag_a;
-  const float* Fb; const uint8_t* flag_b;
+  // sparse force fields (may be null): F[c * qstride + cell] in the compute
+  // type of the storage (double for FP64 storage, float otherwise), one
+  // activity flag per force tile
+  const void* Fa; const uint8_t* flag_a;
+  const void* Fb; const uint8_t* flag_b;
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
 };
 
@@ -54,18 +56,28 @@ void launch_invariants(int storage, const void* fstar, const LBArgs& a,
                        double* out, cudaStream_t s);
 
 // ------------------------------------------------------------ particles
-struct StencilRec {          // one marker's stencil, sorted order, 80 bytes
+// one marker's stencil in sorted order; C is the compute type of the
+// storage (80 bytes for float, 144 for double)
+template <typename C>
+struct StencilRecT {
   int bx, by, bz, kind;      // base node per axis; stencil kind
-  float wx[4], wy[4], wz[4]; // 1-D weights of the nodes base + k
-  float F[3];                // force to spread (already signed and weighted)
-  float pad;
+  C wx[4], wy[4], wz[4];     // 1-D weights of the nodes base + k
+  C F[3];                    // force to spread (already signed and weighted)
+  C pad;
 };
+
+// bytes of one force-field element and of one stencil record
+inline size_t force_elem_bytes(int storage) { return storage == ST_F64 ? 8 : 4; }
+inline size_t stencil_rec_bytes(int storage) {
+  return storage == ST_F64 ? sizeof(StencilRecT<double>) : sizeof(StencilRecT<float>);
+}
 
 struct PartArgs {
   Geom g;
   long long M;
   int stencil;          // 0 trilinear, 1 Peskin 4-point, 2 three-point
   int S;                // nodes per axis: 2, 4, 3
+  int storage;          // selects the compute type of fields and records
 };
 
 // drift / intrinsic force / kick / drift sub-step (see particle_kernels.cu)
@@ -110,22 +122,22 @@ struct GatherArgs {
   // fluid velocity (j + c1 F1 + c2 F2 + cg g) / rho at the stencil nodes
   const void* pops; int storage; float scale16;
   double bb_bot[Q]; double bb_top[Q];
-  const float* F1; const uint8_t* flag1; double c1;
-  const float* F2; const uint8_t* flag2; double c2;
+  const void* F1; const uint8_t* flag1; double c1;
+  const void* F2; const uint8_t* flag2; double c2;
   double cg; double gvec[3]; double rho0_pop;
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
   double* pos; double* aux; double* vel; const double* fint;
   const double* mass; double* fh_out;
-  StencilRec* rec;
+  void* rec;                      // StencilRecT<C>[M]
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
 
 struct SpreadArgs {
-  const StencilRec* rec;
+  const void* rec;                            // StencilRecT<C>[M]
   const int* tile_begin; const int* tile_end;
-  const float* Fin; const uint8_t* flag_in;   // accumulate onto (may be null)
-  float* Fout; uint8_t* flag_out;
+  const void* Fin; const uint8_t* flag_in;    // accumulate onto (may be null)
+  void* Fout; uint8_t* flag_out;
 };
 void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s);
 

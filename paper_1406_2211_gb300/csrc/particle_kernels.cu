@@ -25,45 +25,45 @@ namespace lbc {
 // ------------------------------------------------------------ 1-D stencils
 // phi_4 (Peskin): (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8 on |r| <= 1,
 //                 (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2))/8 on 1 <= |r| <= 2
-__device__ inline float phi4_inner(float a) {
-  return (3.0f - 2.0f * a + sqrtf(fmaxf(0.0f, 1.0f + 4.0f * a - 4.0f * a * a))) * 0.125f;
+template <typename C> __device__ inline C phi4_inner(C a) {
+  return (C(3) - C(2) * a + sqrt(fmax(C(0), C(1) + C(4) * a - C(4) * a * a))) * C(0.125);
 }
-__device__ inline float phi4_outer(float a) {
-  return (5.0f - 2.0f * a - sqrtf(fmaxf(0.0f, -7.0f + 12.0f * a - 4.0f * a * a))) * 0.125f;
+template <typename C> __device__ inline C phi4_outer(C a) {
+  return (C(5) - C(2) * a - sqrt(fmax(C(0), C(-7) + C(12) * a - C(4) * a * a))) * C(0.125);
 }
 // phi_3 (App. A): (1 + sqrt(1 - 3r^2))/3 on |r| <= 1/2,
 //                 (5 - 3|r| - sqrt(-2 + 6|r| - 3r^2))/6 on 1/2 <= |r| <= 3/2
-__device__ inline float phi3_inner(float a) {
-  return (1.0f + sqrtf(fmaxf(0.0f, 1.0f - 3.0f * a * a))) * (1.0f / 3.0f);
+template <typename C> __device__ inline C phi3_inner(C a) {
+  return (C(1) + sqrt(fmax(C(0), C(1) - C(3) * a * a))) / C(3);
 }
-__device__ inline float phi3_outer(float a) {
-  return (5.0f - 3.0f * a - sqrtf(fmaxf(0.0f, -2.0f + 6.0f * a - 3.0f * a * a))) * (1.0f / 6.0f);
+template <typename C> __device__ inline C phi3_outer(C a) {
+  return (C(5) - C(3) * a - sqrt(fmax(C(0), C(-2) + C(6) * a - C(3) * a * a))) / C(6);
 }
 
 // base node b and weights of nodes b + k along one axis for position X
-template <int ST>
-__device__ inline void stencil_1d(double X, int& b, float (&w)[4]) {
+template <int ST, typename C>
+__device__ inline void stencil_1d(double X, int& b, C (&w)[4]) {
   if (ST == 0) {                       // trilinear: nodes floor(X), +1
     const double fl = floor(X);
     b = (int)fl;
-    const float t = (float)(X - fl);
-    w[0] = 1.0f - t; w[1] = t; w[2] = 0.0f; w[3] = 0.0f;
+    const C t = (C)(X - fl);
+    w[0] = C(1) - t; w[1] = t; w[2] = C(0); w[3] = C(0);
   } else if (ST == 1) {                // four-point: floor(X) - 1 .. + 2
     const double fl = floor(X);
     b = (int)fl - 1;
-    const float t = (float)(X - fl);   // r_k = t + 1 - k
-    w[0] = phi4_outer(1.0f + t);
-    w[1] = phi4_inner(t);
-    w[2] = phi4_inner(1.0f - t);
-    w[3] = phi4_outer(2.0f - t);
+    const C t = (C)(X - fl);           // r_k = t + 1 - k
+    w[0] = phi4_outer<C>(C(1) + t);
+    w[1] = phi4_inner<C>(t);
+    w[2] = phi4_inner<C>(C(1) - t);
+    w[3] = phi4_outer<C>(C(2) - t);
   } else {                             // three-point: round(X) - 1 .. + 1
     const double fl = floor(X + 0.5);
     b = (int)fl - 1;
-    const float t = (float)(X - fl);   // in [-1/2, 1/2)
-    w[0] = phi3_outer(1.0f + t);
-    w[1] = phi3_inner(fabsf(t));
-    w[2] = phi3_outer(1.0f - t);
-    w[3] = 0.0f;
+    const C t = (C)(X - fl);           // in [-1/2, 1/2)
+    w[0] = phi3_outer<C>(C(1) + t);
+    w[1] = phi3_inner<C>(fabs(t));
+    w[2] = phi3_outer<C>(C(1) - t);
+    w[3] = C(0);
   }
 }
 
@@ -286,38 +286,41 @@ void launch_tile_ranges(int ntiles, long long M, const uint32_t* keys, int* tb, 
 // ------------------------------------------------------------ gather + couple
 template <typename S, bool WALLS>
 __device__ inline void node_velocity(const GatherArgs& a, const Geom& g, int x, int y, int z,
-                                     float (&u)[3]) {
+                                     typename Store<S>::C (&u)[3]) {
   using C = typename Store<S>::C;
   C f[Q];
   pull_cell<S, WALLS>(static_cast<const S*>(a.pops), g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
-  float rd = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+  C rd = C(0), j0 = C(0), j1 = C(0), j2 = C(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float v = (float)f[i];
+    const C v = f[i];
     rd += v;
-    if (cx_of(i)) j0 += float(cx_of(i)) * v;
-    if (cy_of(i)) j1 += float(cy_of(i)) * v;
-    if (cz_of(i)) j2 += float(cz_of(i)) * v;
+    if (cx_of(i)) j0 += C(cx_of(i)) * v;
+    if (cy_of(i)) j1 += C(cy_of(i)) * v;
+    if (cz_of(i)) j2 += C(cz_of(i)) * v;
   }
   const long long cell = z * g.plane + (long long)y * g.pitch + x;
   const int t = tile_of(g, x, y, z);
-  j0 += float(a.cg * a.gvec[0]);
-  j1 += float(a.cg * a.gvec[1]);
-  j2 += float(a.cg * a.gvec[2]);
-  if (a.F1 && a.flag1[t]) {
-    const float c1 = float(a.c1);
-    j0 += c1 * a.F1[cell]; j1 += c1 * a.F1[g.qstride + cell]; j2 += c1 * a.F1[2 * g.qstride + cell];
+  j0 += C(a.cg * a.gvec[0]);
+  j1 += C(a.cg * a.gvec[1]);
+  j2 += C(a.cg * a.gvec[2]);
+  const C* F1 = static_cast<const C*>(a.F1);
+  const C* F2 = static_cast<const C*>(a.F2);
+  if (F1 && a.flag1[t]) {
+    const C c1 = C(a.c1);
+    j0 += c1 * F1[cell]; j1 += c1 * F1[g.qstride + cell]; j2 += c1 * F1[2 * g.qstride + cell];
   }
-  if (a.F2 && a.flag2[t]) {
-    const float c2 = float(a.c2);
-    j0 += c2 * a.F2[cell]; j1 += c2 * a.F2[g.qstride + cell]; j2 += c2 * a.F2[2 * g.qstride + cell];
+  if (F2 && a.flag2[t]) {
+    const C c2 = C(a.c2);
+    j0 += c2 * F2[cell]; j1 += c2 * F2[g.qstride + cell]; j2 += c2 * F2[2 * g.qstride + cell];
   }
-  const float inv = 1.0f / (float(a.rho0_pop) + rd);
+  const C inv = C(1) / (C(a.rho0_pop) + rd);
   u[0] = j0 * inv; u[1] = j1 * inv; u[2] = j2 * inv;
 }
 
 template <typename S, bool WALLS, int ST>
 __global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const GatherArgs a) {
+  using C = typename Store<S>::C;
   constexpr int SN = nodes_1d<ST>();
   constexpr int NODES = SN * SN * SN;
   constexpr int G = ST == 0 ? 8 : 32;          // lanes per marker
@@ -336,16 +339,16 @@ __global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const Gat
   if (active)
     for (int c = 0; c < 3; ++c) X[c] = P[c * M + i];
   int b[3];
-  float w[3][4];
-  stencil_1d<ST>(X[0], b[0], w[0]);
-  stencil_1d<ST>(X[1], b[1], w[1]);
-  stencil_1d<ST>(X[2], b[2], w[2]);
+  C w[3][4];
+  stencil_1d<ST, C>(X[0], b[0], w[0]);
+  stencil_1d<ST, C>(X[1], b[1], w[1]);
+  stencil_1d<ST, C>(X[2], b[2], w[2]);
 
-  float acc[3] = {0.0f, 0.0f, 0.0f};
+  C acc[3] = {C(0), C(0), C(0)};
   if (active && a.mode != GM_IBM1) {
     for (int n = sub; n < NODES; n += G) {
       const int kx = n % SN, ky = (n / SN) % SN, kz = n / (SN * SN);
-      const float wt = (w[0][kx] * w[1][ky]) * w[2][kz];
+      const C wt = (w[0][kx] * w[1][ky]) * w[2][kz];
       const int xx = wrap_int(b[0] + kx, g.nx);
       const int yy = wrap_int(b[1] + ky, g.ny);
       int zz = b[2] + kz;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const Gat
       } else {
         zz = wrap_int(zz, g.nz);
       }
-      float u[3];
+      C u[3];
       node_velocity<S, WALLS>(a, g, xx, yy, zz, u);
       acc[0] += wt * u[0]; acc[1] += wt * u[1]; acc[2] += wt * u[2];
     }
@@ -422,12 +425,12 @@ __global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const Gat
       break;
   }
   if (a.rec && (a.mode == GM_COUPLE || a.mode == GM_IBM_HALF || a.mode == GM_IBM1)) {
-    StencilRec r;
+    StencilRecT<C> r;
     r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
     for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
-    r.F[0] = (float)Frec[0]; r.F[1] = (float)Frec[1]; r.F[2] = (float)Frec[2];
-    r.pad = 0.0f;
-    a.rec[k] = r;
+    r.F[0] = (C)Frec[0]; r.F[1] = (C)Frec[1]; r.F[2] = (C)Frec[2];
+    r.pad = C(0);
+    static_cast<StencilRecT<C>*>(a.rec)[k] = r;
   }
 }
 
@@ -458,18 +461,16 @@ void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ spreading
-constexpr int SPREAD_WARPS = 4;
-
 // Distinct cells of one axis that a stencil row b, b+1, ... reaches inside
 // [lo, hi] (after periodic wrap), with the weights of coinciding nodes
 // added.  Returns the count.
-template <int SN>
-__device__ inline int axis_hits(int b, const float (&w)[4], int n, bool periodic, int lo, int hi,
-                                int (&loc)[4], float (&wt)[4]) {
+template <int SN, typename C>
+__device__ inline int axis_hits(int b, const C (&w)[4], int n, bool periodic, int lo, int hi,
+                                int (&loc)[4], C (&wt)[4]) {
   int cnt = 0;
 #pragma unroll
   for (int k = 0; k < SN; ++k) {
-    if (w[k] == 0.0f) continue;
+    if (w[k] == C(0)) continue;
     int c = b + k;
     if (periodic) c = wrap_int(c, n);
     else if (c < 0 || c >= n) continue;
@@ -500,16 +501,24 @@ __device__ inline int axis_tiles(int lo, int hi, int n, bool periodic, int (&out
   return cnt;
 }
 
-template <int ST>
-__global__ void __launch_bounds__(SPREAD_WARPS * 32) spread_kernel(const PartArgs p, const SpreadArgs a) {
+// warps per block: 24 KB of shared accumulators either way
+template <typename C> struct SpreadWarps { static constexpr int value = sizeof(C) == 8 ? 2 : 4; };
+
+template <int ST, typename C>
+__global__ void __launch_bounds__(SpreadWarps<C>::value * 32)
+spread_kernel(const PartArgs p, const SpreadArgs a) {
   constexpr int SN = nodes_1d<ST>();
-  __shared__ float sacc[SPREAD_WARPS][3][TILE_CELLS];
+  constexpr int WARPS = SpreadWarps<C>::value;
+  __shared__ C sacc[WARPS][3][TILE_CELLS];
   const Geom& g = p.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float (*acc)[TILE_CELLS] = sacc[wid];
+  C (*acc)[TILE_CELLS] = sacc[wid];
+  const StencilRecT<C>* recs = static_cast<const StencilRecT<C>*>(a.rec);
+  const C* Fin = static_cast<const C*>(a.Fin);
+  C* Fout = static_cast<C*>(a.Fout);
   const int ntiles = g.ntx * g.nty * g.ntz;
-  const long long nwarps = (long long)gridDim.x * SPREAD_WARPS;
-  for (long long tl = (long long)blockIdx.x * SPREAD_WARPS + wid; tl < ntiles; tl += nwarps) {
+  const long long nwarps = (long long)gridDim.x * WARPS;
+  for (long long tl = (long long)blockIdx.x * WARPS + wid; tl < ntiles; tl += nwarps) {
     const int t = (int)tl;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     const int lo[3] = {tx * TILE, ty * TILE, tz * TILE};
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(SPREAD_WARPS * 32) spread_kernel(const PartArg
       const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
       const bool in = x <= hi[0] && y <= hi[1] && z <= hi[2];
       const long long cell = z * g.plane + (long long)y * g.pitch + x;
-      for (int c = 0; c < 3; ++c) acc[c][l] = (carry && in) ? a.Fin[c * g.qstride + cell] : 0.0f;
+      for (int c = 0; c < 3; ++c) acc[c][l] = (carry && in) ? Fin[c * g.qstride + cell] : C(0);
     }
     __syncwarp();
     for (int qz = 0; qz < nt[2]; ++qz)
@@ -543,25 +552,25 @@ __global__ void __launch_bounds__(SPREAD_WARPS * 32) spread_kernel(const PartArg
           const int tn = (lt[2][qz] * g.nty + lt[1][qy]) * g.ntx + lt[0][qx];
           const int kb = a.tile_begin[tn], ke = a.tile_end[tn];
           for (int k = kb; k < ke; ++k) {
-            const StencilRec& r = a.rec[k];
+            const StencilRecT<C>& r = recs[k];
             int lx[4], ly[4], lz[4];
-            float wx[4], wy[4], wz[4];
-            float rw[4];
+            C wx[4], wy[4], wz[4];
+            C rw[4];
             for (int q = 0; q < 4; ++q) rw[q] = r.wx[q];
-            const int cxn = axis_hits<SN>(r.bx, rw, g.nx, true, lo[0], hi[0], lx, wx);
+            const int cxn = axis_hits<SN, C>(r.bx, rw, g.nx, true, lo[0], hi[0], lx, wx);
             if (cxn == 0) continue;
             for (int q = 0; q < 4; ++q) rw[q] = r.wy[q];
-            const int cyn = axis_hits<SN>(r.by, rw, g.ny, true, lo[1], hi[1], ly, wy);
+            const int cyn = axis_hits<SN, C>(r.by, rw, g.ny, true, lo[1], hi[1], ly, wy);
             if (cyn == 0) continue;
             for (int q = 0; q < 4; ++q) rw[q] = r.wz[q];
-            const int czn = axis_hits<SN>(r.bz, rw, g.nz, !g.walls, lo[2], hi[2], lz, wz);
+            const int czn = axis_hits<SN, C>(r.bz, rw, g.nz, !g.walls, lo[2], hi[2], lz, wz);
             if (czn == 0) continue;
-            const float F0 = r.F[0], F1 = r.F[1], F2 = r.F[2];
+            const C F0 = r.F[0], F1 = r.F[1], F2 = r.F[2];
             const int items = cxn * cyn * czn;
             for (int it = lane; it < items; it += 32) {
               const int ix = it % cxn, iy = (it / cxn) % cyn, iz = it / (cxn * cyn);
               const int l = (lz[iz] * TILE + ly[iy]) * TILE + lx[ix];
-              const float wt = (wx[ix] * wy[iy]) * wz[iz];
+              const C wt = (wx[ix] * wy[iy]) * wz[iz];
               acc[0][l] += wt * F0;
               acc[1][l] += wt * F1;
               acc[2][l] += wt * F2;
@@ -573,7 +582,7 @@ __global__ void __launch_bounds__(SPREAD_WARPS * 32) spread_kernel(const PartArg
       const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
       if (x <= hi[0] && y <= hi[1] && z <= hi[2]) {
         const long long cell = z * g.plane + (long long)y * g.pitch + x;
-        for (int c = 0; c < 3; ++c) a.Fout[c * g.qstride + cell] = acc[c][l];
+        for (int c = 0; c < 3; ++c) Fout[c * g.qstride + cell] = acc[c][l];
       }
     }
     if (lane == 0) a.flag_out[t] = 1;
@@ -581,7 +590,9 @@ __global__ void __launch_bounds__(SPREAD_WARPS * 32) spread_kernel(const PartArg
   }
 }
 
-void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
+template <typename C>
+static void spread_c(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
+  constexpr int WARPS = SpreadWarps<C>::value;
   const int ntiles = p.g.ntx * p.g.nty * p.g.ntz;
   static int sms = 0;              // SM count of the first device used
   if (sms == 0) {
@@ -590,12 +601,17 @@ void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     sms = v > 0 ? v : 148;
   }
-  long long want = (ntiles + SPREAD_WARPS - 1) / SPREAD_WARPS;
-  long long cap = (long long)sms * 12;
+  long long want = (ntiles + WARPS - 1) / WARPS;
+  long long cap = (long long)sms * 48 / WARPS;
   const unsigned nb = (unsigned)(want < cap ? want : cap);
-  if (p.stencil == 0) spread_kernel<0><<<nb, SPREAD_WARPS * 32, 0, s>>>(p, a);
-  else if (p.stencil == 1) spread_kernel<1><<<nb, SPREAD_WARPS * 32, 0, s>>>(p, a);
-  else spread_kernel<2><<<nb, SPREAD_WARPS * 32, 0, s>>>(p, a);
+  if (p.stencil == 0) spread_kernel<0, C><<<nb, WARPS * 32, 0, s>>>(p, a);
+  else if (p.stencil == 1) spread_kernel<1, C><<<nb, WARPS * 32, 0, s>>>(p, a);
+  else spread_kernel<2, C><<<nb, WARPS * 32, 0, s>>>(p, a);
+}
+
+void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
+  if (p.storage == ST_F64) spread_c<double>(p, a, s);
+  else spread_c<float>(p, a, s);
 }
 
 // ------------------------------------------------------------ particle momentum

@@ -28,6 +28,7 @@ LBC_NONE, LBC_IBM, LBC_FC, LBC_EBF, LBC_MEBF = 0, 1, 2, 3, 4
 LBC_TRILINEAR, LBC_PESKIN4, LBC_PESKIN3 = 0, 1, 2
 LBC_SPLIT_BASE, LBC_SPLIT_INSIDE, LBC_SPLIT_OUTSIDE = 0, 1, 2
 LBC_OPT_GRAPHS = 1
+LBC_OPT_TIMING = 2
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,
            "bf16dev": LBC_BF16_DEV}
@@ -86,6 +87,7 @@ _PROTOS = {
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
     "lbc_box_launches_per_step": (C.c_int64, [_P]),
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
+    "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
 }
 
 _lib = None
@@ -305,6 +307,13 @@ class Box:
 
     def launches_per_step(self):
         return int(self.lib.lbc_box_launches_per_step(self.handle))
+
+    def lb_timing(self, reset=True):
+        ms = C.c_double()
+        n = C.c_int64()
+        check(self.lib.lbc_box_lb_timing(self.handle, C.byref(ms), C.byref(n), 1 if reset else 0),
+              "lbc_box_lb_timing")
+        return float(ms.value), int(n.value)
 
     def population_bytes(self):
         return int(self.lib.lbc_box_population_bytes(self.handle))

@@ -38,7 +38,9 @@ def test_fluid_steps_match_oracle(shape, coll, tau, lam, g, walls, storage):
                         uw=uw, storage=storage)
     tol = 1e-13 if storage == "f64" else 5e-9
     back = box.get_populations()
-    assert np.abs(back - fbar0).max() < (1e-15 if storage == "f64" else 1e-10)
+    # FP32: one rounding of deviations <= 3.3e-4 (1.5e-11), plus the moving-wall
+    # term added and removed again in FP32 (up to 6e-3, 2.5e-10)
+    assert np.abs(back - fbar0).max() < (1e-15 if storage == "f64" else 1e-9)
     for nsteps in (1, 4, 7):           # 1 eager step, then graph replays + remainder
         box.step(nsteps)
         for _ in range(nsteps):
@@ -50,8 +52,11 @@ def test_fluid_steps_match_oracle(shape, coll, tau, lam, g, walls, storage):
     assert np.abs(u - sm.fluid_velocity()).max() < tol * 20
     mass, mom, st = box.invariants()
     assert st == 0
-    assert abs(mass - sm.mass()) < 1e-9
-    assert np.abs(mom - sm.total_momentum()).max() < 1e-9
+    # FP64 sums of N densities; FP32 deviations carry 2e-11 rounding each
+    assert abs(mass - sm.mass()) < (1e-10 if storage == "f64" else 1e-11 * mass)
+    # FP32: momentum sums of deviations rounded at 6e-8 relative
+    tolp = 1e-12 if storage == "f64" else 1e-7 * max(1.0, np.abs(mom).max())
+    assert np.abs(mom - sm.total_momentum()).max() < tolp
     box.close()
 
 
