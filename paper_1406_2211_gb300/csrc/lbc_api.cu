@@ -238,9 +238,12 @@ struct Plan {
         ++b->timing_used;
       }
     }
-    if (e0) cudaEventRecord(e0, s);
+    // while capturing, the records must become event-record nodes of the
+    // graph (external events), not capture-internal dependencies
+    const unsigned rf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (e0) cudaEventRecordWithFlags(e0, s, rf);
     launch_lb_step(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
-    if (e1) cudaEventRecord(e1, s);
+    if (e1) cudaEventRecordWithFlags(e1, s, rf);
     b->cur = 1 - b->cur;
     ++n;
   }

@@ -205,10 +205,11 @@ CONFIGS = {
         rho0=1.0, kind="fc", gamma=5.0, mass=1.0, stencil="trilinear",
         nchains=2000, beads=50, bond_k=10.0, bond_r0=1.0,
         body_force=(1e-6, 0.0, 0.0), steps=2000, seed=12345,
-        # bond frequency sqrt(4k/m) ~ 6.3 needs particle sub-steps of h/4,
-        # and gamma = 5 is unstable with coupling-only half steps of h/2 once
-        # beads share stencil nodes: Eq. [multistep], n = 2 per half step
-        substeps=2, mode="inside"),
+        # bond frequency sqrt(4k/m) ~ 6.3 needs particle sub-steps below
+        # h/3; gamma = 5 is unstable with coupling-only half steps of h/2
+        # once beads share stencil nodes, and with Eq. [multistep] at n = 2
+        # for the full 2000 chains: Eq. [multistep] with n = 4 (dt = h/8)
+        substeps=4, mode="inside"),
     "cfg3_ibm_shells_192": dict(
         box=(192, 192, 192), collision="bgk", tau=1.0, storage="f32",
         rho0=1.0, kind="ibm", stencil="peskin4", nshells=64, radius=8.0,
