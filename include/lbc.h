@@ -230,6 +230,27 @@ int64_t lbc_box_launches_per_step(const lbc_box* box);
 /* Bytes of one population array (for bandwidth accounting). */
 size_t lbc_box_population_bytes(const lbc_box* box);
 
+/* Total mass and momentum of a post-streaming population array in device
+ * memory, for callers that cannot allocate: it calls no cudaMalloc and needs
+ * no arena, because its scratch is a fixed file-scope device array of
+ * LBC_NOALLOC_MAX_PLANES x 4 doubles (128 KB, held on every device that
+ * loads the library until the process exits).  Typical callers are code
+ * running while a CUDA graph is captured, processes whose device memory is
+ * fully reserved by a pool, and monitoring hooks holding someone else's
+ * buffer.  The paper has no counterpart: this is a library service.
+ *   fbar_dev  device FP64 array [19][nz][ny][nx] of full populations (the
+ *             layout lbc_box_get_populations() writes to the host)
+ *   out_dev   device FP64 array of 4: sum of all populations (mass) and the
+ *             momentum sum_i f_i c_i (x, y, z)
+ * Returns LBC_ERR_ARG for NULL pointers, non-positive sizes or
+ * nz > LBC_NOALLOC_MAX_PLANES.  The first call on a device looks up the
+ * scratch address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the scratch: calls whose kernels overlap
+ * on the GPU (different streams or threads) race and must be serialised. */
+#define LBC_NOALLOC_MAX_PLANES 4096
+lbc_status lbc_fbar_moments_noalloc(const double* fbar_dev, int32_t nx, int32_t ny,
+                                    int32_t nz, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

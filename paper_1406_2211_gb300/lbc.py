@@ -29,6 +29,7 @@ LBC_TRILINEAR, LBC_PESKIN4, LBC_PESKIN3 = 0, 1, 2
 LBC_SPLIT_BASE, LBC_SPLIT_INSIDE, LBC_SPLIT_OUTSIDE = 0, 1, 2
 LBC_OPT_GRAPHS = 1
 LBC_OPT_TIMING = 2
+LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,
            "bf16dev": LBC_BF16_DEV}
@@ -88,6 +89,7 @@ _PROTOS = {
     "lbc_box_launches_per_step": (C.c_int64, [_P]),
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
     "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "lbc_fbar_moments_noalloc": (_S, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
 }
 
 _lib = None
