@@ -71,6 +71,22 @@ __device__ inline C lin_part(C qx, C qy, C qz) {
 }
 
 template <int I> struct IC { static constexpr int value = I; };
+
+// sum_i c_ia c_ib v_i with compile-time coefficients (A, B in 0..2)
+template <typename C, int A, int B, int I = 0>
+__device__ inline C csum(const C (&v)[Q]) {
+  if constexpr (I == Q) {
+    return C(0);
+  } else {
+    constexpr int ca = A == 0 ? cx_of(I) : (A == 1 ? cy_of(I) : cz_of(I));
+    constexpr int cb = B == 0 ? cx_of(I) : (B == 1 ? cy_of(I) : cz_of(I));
+    constexpr int e = ca * cb;
+    C rest = csum<C, A, B, I + 1>(v);
+    if constexpr (e == 0) return rest;
+    else if constexpr (e == 1) return v[I] + rest;
+    else return rest - v[I];
+  }
+}
 template <int I = 0, typename F>
 __device__ inline void unroll_q(F&& f) {
   if constexpr (I < Q) {
@@ -187,6 +203,45 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
     };
     unroll_q(body);
+  } else if (COLL == 2) {
+    // MRT with both ghost groups fully relaxed (their eigenvalue 1 - lambda
+    // is 0): only the bulk and shear moments 4..9 carry non-equilibrium
+    // parts, and they are linear in the stress.  With Pi = sum fbar c c
+    // (deviations) and Pi^eq - rho0 cs2 I = (rd/3) I + rho u0 u0:
+    //   m4 = tr Pi^neq, m5 = 3 Pi^neq_xx - tr, m6 = Pi^neq_yy - Pi^neq_zz,
+    //   m7..9 = Pi^neq_xy, Pi^neq_yz, Pi^neq_xz
+    const C pxx = csum<C, 0, 0>(f), pyy = csum<C, 1, 1>(f), pzz = csum<C, 2, 2>(f);
+    const C pxy = csum<C, 0, 1>(f), pyz = csum<C, 1, 2>(f), pxz = csum<C, 0, 2>(f);
+    const C r3 = div_by<C, 3>(rd);
+    const C nxx = pxx - r3 - rho * u0x * u0x, nyy = pyy - r3 - rho * u0y * u0y;
+    const C nzz = pzz - r3 - rho * u0z * u0z;
+    const C nxy = pxy - rho * u0x * u0y, nyz = pyz - rho * u0y * u0z, nxz = pxz - rho * u0x * u0z;
+    const C tr = nxx + nyy + nzz;
+    const C gb = C(a.gamma_k[0]), gs = C(a.gamma_k[1]);
+    C m[Q];
+    m[4] = tr * (gb * C(1.0 / mrt_b(4)));
+    m[5] = (C(3) * nxx - tr) * (gs * C(1.0 / mrt_b(5)));
+    m[6] = (nyy - nzz) * (gs * C(1.0 / mrt_b(6)));
+    m[7] = nxy * (gs * C(1.0 / mrt_b(7)));
+    m[8] = nyz * (gs * C(1.0 / mrt_b(8)));
+    m[9] = nxz * (gs * C(1.0 / mrt_b(9)));
+    const C md = div_by<C, 36>(rd);
+    const C j1x = div_by<C, 12>(jx + Fx), j1y = div_by<C, 12>(jy + Fy), j1z = div_by<C, 12>(jz + Fz);
+    auto out = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      C post = C(0);
+      if constexpr (mrt_e(4, i) != 0) post += C(mrt_e(4, i)) * m[4];
+      if constexpr (mrt_e(5, i) != 0) post += C(mrt_e(5, i)) * m[5];
+      if constexpr (mrt_e(6, i) != 0) post += C(mrt_e(6, i)) * m[6];
+      if constexpr (mrt_e(7, i) != 0) post += C(mrt_e(7, i)) * m[7];
+      if constexpr (mrt_e(8, i) != 0) post += C(mrt_e(8, i)) * m[8];
+      if constexpr (mrt_e(9, i) != 0) post += C(mrt_e(9, i)) * m[9];
+      const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
+                                rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) +
+                  C(w_of(i)) * post;
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+    };
+    unroll_q(out);
   } else {
     // neq_i = fbar_i - f_i^eq(rho, u0); relax per moment; add f^eq(rho, u1)
     const C md = div_by<C, 36>(rd);
@@ -232,6 +287,9 @@ static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream
   if (a.collision == 0) {
     if (a.g.walls) { if (forced) LBC_LAUNCH(0, true, true); else LBC_LAUNCH(0, true, false); }
     else { if (forced) LBC_LAUNCH(0, false, true); else LBC_LAUNCH(0, false, false); }
+  } else if (a.gamma_k[2] == 0.0 && a.gamma_k[3] == 0.0) {
+    if (a.g.walls) { if (forced) LBC_LAUNCH(2, true, true); else LBC_LAUNCH(2, true, false); }
+    else { if (forced) LBC_LAUNCH(2, false, true); else LBC_LAUNCH(2, false, false); }
   } else {
     if (a.g.walls) { if (forced) LBC_LAUNCH(1, true, true); else LBC_LAUNCH(1, true, false); }
     else { if (forced) LBC_LAUNCH(1, false, true); else LBC_LAUNCH(1, false, false); }

@@ -62,8 +62,9 @@ struct Layout {
   size_t off_pos[2], off_vel[2], off_fint, off_fh, off_aux, off_mass, off_ext;
   size_t off_key[2], off_idx[2], off_hist, off_tb, off_te, off_rec;
   size_t off_nbr_start, off_nbr_j, off_nbr_k, off_nbr_r0;
+  size_t off_inv_mass, off_reach, off_ntab, off_status;
   size_t off_red, off_redout;
-  int ntiles;
+  int ntiles, maxnt;
   bool has_particles;
 };
 
@@ -110,6 +111,11 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_nbr_j = take(nb2 * 4);
     L.off_nbr_k = take(nb2 * 8);
     L.off_nbr_r0 = take(nb2 * 8);
+    L.off_inv_mass = take((size_t)M * sizeof(double));
+    L.off_reach = take((size_t)M * sizeof(short4));
+    L.maxnt = g.ntx > g.nty ? (g.ntx > g.ntz ? g.ntx : g.ntz) : (g.nty > g.ntz ? g.nty : g.ntz);
+    L.off_ntab = take((size_t)3 * L.maxnt * 8 * sizeof(int));
+    L.off_status = take(sizeof(int));
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
@@ -251,8 +257,9 @@ struct Plan {
   // drift / intrinsic forces / kick / drift; input the current particle
   // buffer, output the other one (flips pc) unless positions are not written
   void drift(double pre, double kick, double post, bool force, bool key, bool write = true,
-             const double* pos_in = nullptr) {
+             const double* pos_in = nullptr, double pre0 = 0.0) {
     DriftArgs d{};
+    d.dt_pre0 = pre0;
     d.dt_pre = pre; d.dt_kick = kick; d.dt_post = post;
     d.compute_force = force ? 1 : 0;
     d.write_key = key ? 1 : 0;
@@ -263,7 +270,7 @@ struct Plan {
     d.fint_out = force ? b->dptr(b->L.off_fint) : nullptr;
     d.key_out = b->uptr(b->L.off_key[0]);
     d.idx_out = b->uptr(b->L.off_idx[0]);
-    d.mass = b->dptr(b->L.off_mass);
+    d.inv_mass = b->dptr(b->L.off_inv_mass);
     d.ext = b->dptr(b->L.off_ext);
     d.nbr_start = b->iptr(b->L.off_nbr_start);
     d.nbr_j = b->iptr(b->L.off_nbr_j);
@@ -271,7 +278,7 @@ struct Plan {
     d.nbr_r0 = b->dptr(b->L.off_nbr_r0);
     launch_drift(part_args(b), d, s);
     if (write) b->pc = 1 - b->pc;
-    b->sorted = false;
+    if (key) b->sorted = false;
     ++n;
   }
 
@@ -307,9 +314,12 @@ struct Plan {
     a.vel = b->dptr(b->L.off_vel[b->pc]);
     a.aux = b->dptr(b->L.off_aux);
     a.fint = b->dptr(b->L.off_fint);
-    a.mass = b->dptr(b->L.off_mass);
+    a.inv_mass = b->dptr(b->L.off_inv_mass);
     a.fh_out = b->dptr(b->L.off_fh);
     a.rec = b->arena + b->L.off_rec;
+    a.reach = reinterpret_cast<short4*>(b->arena + b->L.off_reach);
+    a.keys = b->uptr(b->L.off_key[0]);
+    a.status = b->iptr(b->L.off_status);
     return a;
   }
 
@@ -327,6 +337,9 @@ struct Plan {
   void spread(int out, bool carry) {
     SpreadArgs a{};
     a.rec = b->arena + b->L.off_rec;
+    a.reach = reinterpret_cast<const short4*>(b->arena + b->L.off_reach);
+    a.ntab = b->iptr(b->L.off_ntab);
+    a.maxnt = b->L.maxnt;
     a.tile_begin = b->iptr(b->L.off_tb);
     a.tile_end = b->iptr(b->L.off_te);
     a.Fin = carry ? b->F(out) : nullptr;
@@ -427,14 +440,21 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     P.spread(ia, false);
     P.drift(0.5 * h, 0.0, 0.0, false, false);
   } else if (split == LBC_SPLIT_INSIDE) {
-    // Eq. [multistep]: n Verlet sub-steps with coupling on each side of LB
+    // Eq. [multistep]: n Verlet sub-steps with coupling on each side of LB.
+    // Markers are binned once, at the first sub-step; the trailing half
+    // drift of a sub-step and the leading half drift of the next one run in
+    // one kernel (the same two FP64 updates in the same order).
     const int n = b->cpl.substeps;
     const double dt = 0.5 * h / n;
     for (int half = 0; half < 2; ++half) {
       const int out = half == 0 ? ib : ia;
       for (int k = 0; k < n; ++k) {
-        P.drift(0.5 * dt, 0.0, 0.0, true, true);
-        P.sort();
+        if (half == 0 && k == 0) {
+          P.drift(0.5 * dt, 0.0, 0.0, true, true);
+          P.sort();
+        } else {
+          P.drift(0.5 * dt, 0.0, 0.0, true, false, true, nullptr, 0.5 * dt);
+        }
         GatherArgs a = P.gather_base();
         a.mode = GM_COUPLE; a.s = dt; a.include_int = 1; a.rec_weight = 1.0 / n;
         const double gfrac = 0.5 * h * double(k) / n;
@@ -444,10 +464,10 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
           P.fields(a, k > 0 ? ia : -1, 0.5 * h, -1, 0.0, gfrac);
         P.gather(a);
         P.spread(out, k > 0);
-        P.drift(0.5 * dt, 0.0, 0.0, false, false);
       }
       if (half == 0) P.lb(b->F(ia), b->F(ib), 0.5 * h, 0.5 * h, h);
     }
+    P.drift(0.5 * dt, 0.0, 0.0, false, false);
   } else {
     // Sec. 6 split with the coupling outside: F_h^1/2 [P F_int P]^n LB
     // [P F_int P]^n F_h^1/2
@@ -729,6 +749,16 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->launches = 0;
   fill_lb_args(b);
   cudaStream_t s = S(stream);
+  if (L.has_particles) {
+    std::vector<int> tab((size_t)3 * L.maxnt * 8);
+    neighbour_tiles(L.g, L.maxnt, tab.data());
+    if (cudaMemcpy(b->iptr(L.off_ntab), tab.data(), tab.size() * sizeof(int),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess) {
+      delete b;
+      return LBC_ERR_CUDA;
+    }
+  }
   lbc_status st = clear_pending(b, s);
   if (st == LBC_OK) {
     const double u0[3] = {0.0, 0.0, 0.0};
@@ -862,9 +892,9 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
       if (p->vel) vel[c * M + i] = p->vel[3 * i + c];
       if (p->ext_force) ext[c * M + i] = p->ext_force[3 * i + c];
     }
-  if (p->mass)
+  if (p->mass && b->cpl.kind != LBC_IBM)
     for (int64_t i = 0; i < M; ++i) {
-      if (!(p->mass[i] > 0.0) && b->cpl.kind != LBC_IBM) return LBC_ERR_ARG;
+      if (!(p->mass[i] > 0.0)) return LBC_ERR_ARG;
       mass[i] = p->mass[i];
     }
   // bonds as a per-particle adjacency list (CSR), in bond order
@@ -890,6 +920,11 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   CK(cudaMemcpyAsync(b->dptr(b->L.off_pos[0]), pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->dptr(b->L.off_vel[0]), vel.data(), vel.size() * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->dptr(b->L.off_mass), mass.data(), mass.size() * 8, cudaMemcpyHostToDevice, s));
+  std::vector<double> inv_mass(M);
+  for (int64_t i = 0; i < M; ++i) inv_mass[i] = 1.0 / mass[i];
+  CK(cudaMemcpyAsync(b->dptr(b->L.off_inv_mass), inv_mass.data(), inv_mass.size() * 8,
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(b->iptr(b->L.off_status), 0, sizeof(int), s));
   CK(cudaMemcpyAsync(b->dptr(b->L.off_ext), ext.data(), ext.size() * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->dptr(b->L.off_fh), 0, 3 * M * 8, s));
   CK(cudaMemsetAsync(b->dptr(b->L.off_fint), 0, 3 * M * 8, s));
@@ -958,8 +993,13 @@ lbc_status lbc_box_invariants(lbc_box* b, double* mass, double* momentum, void* 
   const bool pm = particles(b) && b->cpl.kind != LBC_IBM;
   if (pm) launch_particle_momentum(b->M, b->dptr(b->L.off_vel[b->pc]), b->dptr(b->L.off_mass), out + 8, s);
   double h[16] = {0};
+  int drift_flag = 0;
   CK(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (b->L.has_particles)
+    CK(cudaMemcpyAsync(&drift_flag, b->iptr(b->L.off_status), sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  // a marker left its bin (moved more than a cell within one step)
+  if (drift_flag && b->status == LBC_OK) b->status = LBC_ERR_STATE;
   CK(cudaGetLastError());
   const Geom& g = b->L.g;
   if (mass) *mass = (double)g.nx * g.ny * g.nz * b->lat.rho0 + h[0];

@@ -99,9 +99,11 @@ __device__ inline double wrap_coord(double X, int n) {
   return r;
 }
 
+// v into [0, n) for v within a few n of the box (no integer division)
 __device__ inline int wrap_int(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
 }
 
 }  // namespace lbc

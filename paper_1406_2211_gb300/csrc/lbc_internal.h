@@ -80,16 +80,18 @@ struct PartArgs {
   int storage;          // selects the compute type of fields and records
 };
 
-// drift / intrinsic force / kick / drift sub-step (see particle_kernels.cu)
+// drift / intrinsic force / kick / drift sub-step (see particle_kernels.cu):
+//   r <- wrap(wrap(r + dt_pre0 v) + dt_pre v); F = F_int(r);
+//   v <- v + dt_kick F / m; r <- wrap(r + dt_post v)
 struct DriftArgs {
-  double dt_pre, dt_kick, dt_post;
+  double dt_pre0, dt_pre, dt_kick, dt_post;
   int compute_force;     // evaluate F_int at the pre-drifted positions
   int write_key;         // tile key of the final positions
   const double* pos_in; const double* vel_in;   // [3][M]
   double* pos_out; double* vel_out;             // may alias nothing
   double* fint_out;                              // [3][M] or null
   uint32_t* key_out; uint32_t* idx_out;
-  const double* mass; const double* ext;        // ext [3][M] or null
+  const double* inv_mass; const double* ext;    // ext [3][M]
   const int* nbr_start; const int* nbr_j;
   const double* nbr_k; const double* nbr_r0;
 };
@@ -127,18 +129,27 @@ struct GatherArgs {
   double cg; double gvec[3]; double rho0_pop;
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
+  const uint32_t* keys;           // sorted home tile of each slot (null: no check)
   double* pos; double* aux; double* vel; const double* fint;
-  const double* mass; double* fh_out;
-  void* rec;                      // StencilRecT<C>[M]
+  const double* inv_mass; double* fh_out;
+  void* rec;                      // StencilRecT<C>[M], by sorted slot
+  short4* reach;                  // stencil base per sorted slot (x, y, z)
+  int* status;                    // set to 1 if a marker left its home tile +- 1 cell
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
 
 struct SpreadArgs {
   const void* rec;                            // StencilRecT<C>[M]
+  const short4* reach;                        // stencil base per sorted slot
   const int* tile_begin; const int* tile_end;
+  // per axis and tile, the (up to 4) tiles holding markers whose stencil can
+  // reach it: ntab[(axis * maxnt + t) * 4 + q], -1 padded
+  const int* ntab; int maxnt;
   const void* Fin; const uint8_t* flag_in;    // accumulate onto (may be null)
   void* Fout; uint8_t* flag_out;
 };
+// host: fill the neighbour-tile table (3 * maxnt * 4 ints)
+void neighbour_tiles(const Geom& g, int maxnt, int* table);
 void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s);
 
 // particle momentum sum m v (FP64), one block

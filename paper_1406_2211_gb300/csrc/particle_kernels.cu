@@ -10,14 +10,22 @@
 // hydrodynamic velocity (sum fbar c + pending half forces) / rho of Sec. 4.
 //
 // Coupling update (Sec. 5.2, Eq. [modified-force]; Sec. 5.3,
-// Eqs. [ebf], [modified-ebf]) is evaluated per particle in FP64.
+// Eqs. [ebf], [modified-ebf]).  Positions and velocities are integrated in
+// FP64; forces and the coupling arithmetic use the compute type C of the
+// population storage (double for FP64 storage, float otherwise), because
+// FP64 arithmetic is a small fraction of the FP32 rate on this GPU.
 //
 // Spreading is a gather over force tiles of 8^3 cells: one warp owns one
-// tile, walks the markers whose stencil can reach it (markers are sorted by
-// tile, so they come from a handful of contiguous ranges) in a fixed order
-// and accumulates into shared memory; every node of a tile is written by one
-// lane per marker, so no atomics are used and the summation order does not
-// depend on scheduling or on what else runs on the GPU.
+// tile, scans the markers binned into the neighbouring tiles 32 at a time
+// with a cheap reach test on their stencil base (ballot), and accumulates the
+// survivors one after another into shared memory; every node of a tile is
+// written by one lane per marker, so no atomics are used and the summation
+// order is fixed (markers sorted by tile, tiles in a fixed order).
+//
+// Markers are binned once per step; the bins stay valid while a marker is
+// within one cell of its home tile (a marker moves |v| h << 1 per step in
+// any lattice-Boltzmann regime).  The interpolation kernel checks this and
+// raises a status flag if it is violated.
 #include "lb_device.cuh"
 
 namespace lbc {
@@ -69,61 +77,86 @@ __device__ inline void stencil_1d(double X, int& b, C (&w)[4]) {
 
 template <int ST> __host__ __device__ constexpr int nodes_1d() { return ST == 0 ? 2 : (ST == 1 ? 4 : 3); }
 
-// ------------------------------------------------------------ drift / forces
+// ------------------------------------------------------------ periodic helpers
+// X into [0, n) for X in (-n, 2n): the same result as r = fmod(X, n), + n if
+// negative, - n if that rounded up to n, without the FP64 fmod
 __device__ inline double wrap_axis(double X, int n, bool periodic) {
-  return periodic ? wrap_coord(X, n) : X;
+  if (!periodic) return X;
+  const double dn = (double)n;
+  if (X < 0.0) X += dn;
+  else if (X >= dn) X -= dn;
+  if (X >= dn) X -= dn;
+  return X;
+}
+
+// minimum image of a separation d (|d| < 1.5 n); ties at |d| = n/2 are kept,
+// as rint(d/n) = 0 there
+__device__ inline double min_image(double d, int n, bool periodic) {
+  if (!periodic) return d;
+  const double h = 0.5 * n;
+  if (d > h) d -= n;
+  else if (d < -h) d += n;
+  return d;
 }
 
 __device__ inline uint32_t key_of(const Geom& g, double x, double y, double z) {
-  int ix = (int)floor(x), iy = (int)floor(y), iz = (int)floor(z);
-  ix = ix < 0 ? 0 : (ix >= g.nx ? g.nx - 1 : ix);
-  iy = iy < 0 ? 0 : (iy >= g.ny ? g.ny - 1 : iy);
-  iz = iz < 0 ? 0 : (iz >= g.nz ? g.nz - 1 : iz);
+  int ix = wrap_int((int)floor(x), g.nx), iy = wrap_int((int)floor(y), g.ny);
+  int iz = (int)floor(z);
+  if (g.walls) iz = iz < 0 ? 0 : (iz >= g.nz ? g.nz - 1 : iz);
+  else iz = wrap_int(iz, g.nz);
   return (uint32_t)tile_of(g, ix, iy, iz);
 }
 
-__global__ void drift_kernel(const PartArgs p, const DriftArgs d) {
+// ------------------------------------------------------------ drift / forces
+template <typename C>
+__global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const DriftArgs d) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= p.M) return;
   const long long M = p.M;
   const Geom& g = p.g;
   const int n3[3] = {g.nx, g.ny, g.nz};
   const bool per[3] = {true, true, !g.walls};
+  // intermediate positions are left unwrapped (they stay within a cell of
+  // the box); only the final position is wrapped, and bond vectors use the
+  // minimum image, so no FP64 work is spent on wrapping in between
   double r1[3], v[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     v[c] = d.vel_in[c * M + i];
-    r1[c] = wrap_axis(d.pos_in[c * M + i] + d.dt_pre * v[c], n3[c], per[c]);
+    r1[c] = (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
   }
-  double F[3] = {0.0, 0.0, 0.0};
+  C F[3] = {C(0), C(0), C(0)};
   if (d.compute_force) {
-    if (d.ext) {
-      for (int c = 0; c < 3; ++c) F[c] = d.ext[c * M + i];
-    }
-    const int bbeg = d.nbr_start ? d.nbr_start[i] : 0, bend = d.nbr_start ? d.nbr_start[i + 1] : 0;
+    for (int c = 0; c < 3; ++c) F[c] = (C)d.ext[c * M + i];
+    const int bbeg = d.nbr_start[i], bend = d.nbr_start[i + 1];
     for (int b = bbeg; b < bend; ++b) {
       const long long j = d.nbr_j[b];
-      double dd[3], dist2 = 0.0;
+      double e[3];
+      double dist2 = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double rj = wrap_axis(d.pos_in[c * M + j] + d.dt_pre * d.vel_in[c * M + j], n3[c], per[c]);
-        double e = rj - r1[c];
-        if (per[c]) e -= n3[c] * rint(e / n3[c]);
-        dd[c] = e;
-        dist2 += e * e;
+        const double vj = d.vel_in[c * M + j];
+        const double rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
+        e[c] = min_image(rj - r1[c], n3[c], per[c]);
+        dist2 += e[c] * e[c];
       }
-      const double dist = sqrt(dist2);
-      const double mag = d.nbr_k[b] * (dist - d.nbr_r0[b]) / dist;
-      for (int c = 0; c < 3; ++c) F[c] += dd[c] * mag;
+      // stretch |d| - r0 = (|d|^2 - r0^2) / (|d| + r0): the difference of
+      // squares in FP64 (bonds sit near their rest length, where |d| - r0
+      // formed in FP32 would lose most of its digits), the rest in C
+      const double r0 = d.nbr_r0[b];
+      const C dist = sqrt((C)dist2);
+      const C stretch = (C)(dist2 - r0 * r0) / (dist + (C)r0);
+      const C mag = C(d.nbr_k[b]) * stretch / dist;
+      for (int c = 0; c < 3; ++c) F[c] += (C)e[c] * mag;
     }
     if (d.fint_out)
-      for (int c = 0; c < 3; ++c) d.fint_out[c * M + i] = F[c];
+      for (int c = 0; c < 3; ++c) d.fint_out[c * M + i] = (double)F[c];
   }
-  const double kick = d.dt_kick / d.mass[i];
+  const double kick = d.dt_kick * d.inv_mass[i];
   double r2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    v[c] += kick * F[c];
+    v[c] += kick * (double)F[c];
     r2[c] = wrap_axis(r1[c] + d.dt_post * v[c], n3[c], per[c]);
   }
   if (d.pos_out)
@@ -139,7 +172,9 @@ __global__ void drift_kernel(const PartArgs p, const DriftArgs d) {
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
   if (p.M == 0) return;
   const int bs = 128;
-  drift_kernel<<<(unsigned)((p.M + bs - 1) / bs), bs, 0, s>>>(p, d);
+  const unsigned nb = (unsigned)((p.M + bs - 1) / bs);
+  if (p.storage == ST_F64) drift_kernel<double><<<nb, bs, 0, s>>>(p, d);
+  else drift_kernel<float><<<nb, bs, 0, s>>>(p, d);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -148,7 +183,7 @@ void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
 // (digit, block), and a stable scatter that ranks equal digits in element
 // order (warp match within rounds of 256 elements).
 constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 4;
+constexpr int SORT_ITEMS = 8;
 constexpr int SORT_BLOCK = SORT_THREADS * SORT_ITEMS;
 
 static int sort_blocks(long long M) { return (int)((M + SORT_BLOCK - 1) / SORT_BLOCK); }
@@ -169,9 +204,10 @@ sort_hist_kernel(const uint32_t* __restrict__ keys, long long M, int shift, int*
   hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive scan of n ints in place, one block of 1024 threads
+// exclusive scan of n ints in place, one block of 1024 threads: each thread
+// sums a contiguous chunk, the chunk sums are scanned with warp shuffles
 __global__ void __launch_bounds__(1024) scan_kernel(int* data, int n) {
-  __shared__ int part[1024];
+  __shared__ int wsum[32];
   const int per = (n + 1023) / 1024;
   const int lo = threadIdx.x * per;
   int sum = 0;
@@ -179,15 +215,24 @@ __global__ void __launch_bounds__(1024) scan_kernel(int* data, int n) {
     const int e = lo + k;
     if (e < n) sum += data[e];
   }
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = sum;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
   }
-  int run = part[threadIdx.x] - sum;     // exclusive prefix of this chunk
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = wsum[lane];
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += v;
+    }
+    wsum[lane] = w;                      // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - sum + (wid > 0 ? wsum[wid - 1] : 0);
   for (int k = 0; k < per; ++k) {
     const int e = lo + k;
     if (e < n) {
@@ -318,108 +363,125 @@ __device__ inline void node_velocity(const GatherArgs& a, const Geom& g, int x, 
   u[0] = j0 * inv; u[1] = j1 * inv; u[2] = j2 * inv;
 }
 
+// is cell c within [lo - 1, hi + 1] of its home tile (periodic wrap)?
+__device__ inline bool near_home(int c, int lo, int hi, int n, bool periodic) {
+  if (!periodic) return c >= lo - 1 && c <= hi + 1;
+  if (n <= 3 * TILE) return true;      // the search window spans the whole axis
+  int d = c - lo;
+  if (d < -n / 2) d += n;
+  else if (d >= n - n / 2) d -= n;
+  return d >= -1 && d <= hi - lo + 1;
+}
+
+// One marker per lane (sorted slot k): the position is turned into a
+// stencil base and fraction, the lane walks the stencil nodes itself (their
+// loads are independent, so many are in flight per warp) and then does the
+// FP64 coupling update of its own marker.
 template <typename S, bool WALLS, int ST>
-__global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const GatherArgs a) {
+__global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const GatherArgs a) {
   using C = typename Store<S>::C;
   constexpr int SN = nodes_1d<ST>();
-  constexpr int NODES = SN * SN * SN;
-  constexpr int G = ST == 0 ? 8 : 32;          // lanes per marker
   const Geom& g = p.g;
   const long long M = p.M;
-  const int lane = threadIdx.x & 31;
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long k = gw * (32 / G) + lane / G;
-  const int sub = lane % G;
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool active = k < M;
-  const long long i = active ? (a.perm ? (long long)a.perm[k] : k) : 0;
+  if (!active) return;
+  const long long i = a.perm ? (long long)a.perm[k] : k;
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const bool per[3] = {true, true, !g.walls};
 
   const bool at_aux = a.mode == GM_IBM_HALF || a.mode == GM_IBM_FINAL;
   const double* P = at_aux ? a.aux : a.pos;
-  double X[3] = {0.0, 0.0, 0.0};
-  if (active)
-    for (int c = 0; c < 3; ++c) X[c] = P[c * M + i];
   int b[3];
   C w[3][4];
-  stencil_1d<ST, C>(X[0], b[0], w[0]);
-  stencil_1d<ST, C>(X[1], b[1], w[1]);
-  stencil_1d<ST, C>(X[2], b[2], w[2]);
+  double X[3];
+  for (int c = 0; c < 3; ++c) {
+    X[c] = P[c * M + i];
+    stencil_1d<ST, C>(X[c], b[c], w[c]);
+  }
 
-  C acc[3] = {C(0), C(0), C(0)};
-  if (active && a.mode != GM_IBM1) {
-    for (int n = sub; n < NODES; n += G) {
-      const int kx = n % SN, ky = (n / SN) % SN, kz = n / (SN * SN);
-      const C wt = (w[0][kx] * w[1][ky]) * w[2][kz];
-      const int xx = wrap_int(b[0] + kx, g.nx);
-      const int yy = wrap_int(b[1] + ky, g.ny);
+  C own[3] = {C(0), C(0), C(0)};
+  if (a.mode != GM_IBM1) {
+    int xs[SN], ys[SN];
+#pragma unroll
+    for (int q = 0; q < SN; ++q) {
+      xs[q] = wrap_int(b[0] + q, g.nx);
+      ys[q] = wrap_int(b[1] + q, g.ny);
+    }
+#pragma unroll 1
+    for (int kz = 0; kz < SN; ++kz) {
       int zz = b[2] + kz;
       if (WALLS) {
         if (zz < 0 || zz >= g.nz) continue;
       } else {
         zz = wrap_int(zz, g.nz);
       }
-      C u[3];
-      node_velocity<S, WALLS>(a, g, xx, yy, zz, u);
-      acc[0] += wt * u[0]; acc[1] += wt * u[1]; acc[2] += wt * u[2];
-    }
-  }
-#pragma unroll
-  for (int off = G / 2; off > 0; off >>= 1) {
-    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], off);
-    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], off);
-    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], off);
-  }
-  if (!active || sub != 0) return;
-
-  const double u[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  double Frec[3] = {0.0, 0.0, 0.0};
-  const double s = a.s;
-  switch (a.mode) {
-    case GM_COUPLE: {
-      const double m = a.mass[i];
-      double v[3], Fi[3];
-      for (int c = 0; c < 3; ++c) {
-        v[c] = a.vel[c * M + i];
-        Fi[c] = (a.include_int && a.fint) ? a.fint[c * M + i] : 0.0;
-      }
-      double Fh[3];
-      if (a.kind == 4) {                      // modified EBF, Eq. [modified-ebf]
-        const double r = 1.0 / (1.0 + m / a.rho0);
-        const double inv = 1.0 / (s * (1.0 / m + 1.0 / a.rho0));
-        for (int c = 0; c < 3; ++c) Fh[c] = -(v[c] - u[c]) * inv - r * Fi[c];
-      } else {
-        const double gam = a.kind == 3 ? a.rho0 : a.gamma;   // EBF: rho a^3 / h
-        if (a.order == 1) {
-          for (int c = 0; c < 3; ++c) Fh[c] = -gam * (v[c] - u[c]);
-        } else {                              // Crank-Nicolson, Eq. [modified-force]
-          const double al = gam * s / m, be = gam * s / a.rho0;
-          const double D = 1.0 + 0.5 * al + 0.5 * be;
-          for (int c = 0; c < 3; ++c) Fh[c] = -(gam * (v[c] - u[c]) + 0.5 * al * Fi[c]) / D;
+#pragma unroll 1
+      for (int ky = 0; ky < SN; ++ky) {
+        const C wyz = w[1][ky] * w[2][kz];
+#pragma unroll 2
+        for (int kx = 0; kx < SN; ++kx) {
+          C u[3];
+          node_velocity<S, WALLS>(a, g, xs[kx], ys[ky], zz, u);
+          const C wt = w[0][kx] * wyz;
+          own[0] += wt * u[0]; own[1] += wt * u[1]; own[2] += wt * u[2];
         }
       }
-      const double kick = s / m;
+    }
+  }
+
+  // ---- own marker: coupling / advection update (FP64 integration)
+  const double s = a.s;
+  C Frec[3] = {C(0), C(0), C(0)};
+  switch (a.mode) {
+    case GM_COUPLE: {
+      const double im = a.inv_mass[i];
+      C dv[3], Fi[3];
+      double v[3];
       for (int c = 0; c < 3; ++c) {
-        a.vel[c * M + i] = v[c] + kick * (Fh[c] + Fi[c]);
-        if (a.fh_out) a.fh_out[c * M + i] = Fh[c];
-        Frec[c] = -a.rec_weight * Fh[c];
+        v[c] = a.vel[c * M + i];
+        dv[c] = (C)(v[c] - (double)own[c]);
+        Fi[c] = a.include_int ? (C)a.fint[c * M + i] : C(0);
+      }
+      C Fh[3];
+      const C cs = C(s), cim = C(im), crho = C(a.rho0);
+      if (a.kind == 4) {                      // modified EBF, Eq. [modified-ebf]
+        // r = 1/(1 + m/rho0) = rho0 im/(rho0 im + 1); 1/(s(1/m + 1/rho0))
+        const C r = crho * cim / (crho * cim + C(1));
+        const C inv = C(1) / (cs * (cim + C(1) / crho));
+        for (int c = 0; c < 3; ++c) Fh[c] = -dv[c] * inv - r * Fi[c];
+      } else {
+        const C gam = a.kind == 3 ? crho : C(a.gamma);   // EBF: rho a^3 / h
+        if (a.order == 1) {
+          for (int c = 0; c < 3; ++c) Fh[c] = -gam * dv[c];
+        } else {                              // Crank-Nicolson, Eq. [modified-force]
+          const C al = gam * cs * cim, be = gam * cs / crho;
+          const C D = C(1) + C(0.5) * al + C(0.5) * be;
+          for (int c = 0; c < 3; ++c) Fh[c] = -(gam * dv[c] + C(0.5) * al * Fi[c]) / D;
+        }
+      }
+      const double kick = s * im;
+      for (int c = 0; c < 3; ++c) {
+        a.vel[c * M + i] = v[c] + kick * (double)(Fh[c] + Fi[c]);
+        if (a.fh_out) a.fh_out[c * M + i] = (double)Fh[c];
+        Frec[c] = -C(a.rec_weight) * Fh[c];
       }
       break;
     }
     case GM_IBM_PREDICT:
       for (int c = 0; c < 3; ++c)
-        a.aux[c * M + i] = wrap_axis(a.pos[c * M + i] + s * u[c], c == 0 ? g.nx : (c == 1 ? g.ny : g.nz),
-                                     c < 2 || !g.walls);
+        a.aux[c * M + i] = wrap_axis(a.pos[c * M + i] + s * (double)own[c], n3[c], per[c]);
       break;
     case GM_IBM_HALF:
     case GM_IBM_FINAL:
     case GM_ADVECT:
       for (int c = 0; c < 3; ++c)
-        a.pos[c * M + i] = wrap_axis(a.pos[c * M + i] + s * u[c], c == 0 ? g.nx : (c == 1 ? g.ny : g.nz),
-                                     c < 2 || !g.walls);
+        a.pos[c * M + i] = wrap_axis(a.pos[c * M + i] + s * (double)own[c], n3[c], per[c]);
       if (a.mode == GM_IBM_HALF)
-        for (int c = 0; c < 3; ++c) Frec[c] = a.rec_weight * a.fint[c * M + i];
+        for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * (C)a.fint[c * M + i];
       break;
     case GM_IBM1:
-      for (int c = 0; c < 3; ++c) Frec[c] = a.rec_weight * a.fint[c * M + i];
+      for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * (C)a.fint[c * M + i];
       break;
     default:
       break;
@@ -428,18 +490,31 @@ __global__ void __launch_bounds__(128) gather_kernel(const PartArgs p, const Gat
     StencilRecT<C> r;
     r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
     for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
-    r.F[0] = (C)Frec[0]; r.F[1] = (C)Frec[1]; r.F[2] = (C)Frec[2];
+    r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
     r.pad = C(0);
     static_cast<StencilRecT<C>*>(a.rec)[k] = r;
+    a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+    if (a.keys) {
+      // the bins of this step are valid while the marker stays within one
+      // cell of its home tile
+      const int t = (int)a.keys[k];
+      const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+      bool ok = true;
+      for (int c = 0; c < 3; ++c) {
+        int cell = (int)floor(X[c]);
+        if (!per[c]) cell = cell < 0 ? 0 : (cell >= n3[c] ? n3[c] - 1 : cell);
+        const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
+        ok = ok && near_home(cell, lo, hi, n3[c], per[c]);
+      }
+      if (!ok) *a.status = 1;
+    }
   }
 }
 
 template <typename S, bool WALLS>
 static void gather_st(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
-  const int G = p.stencil == 0 ? 8 : 32;
-  const long long lanes = p.M * G;
-  const int bs = 128;
-  const unsigned nb = (unsigned)((lanes + bs - 1) / bs);
+  const int bs = 128;                          // one marker per thread
+  const unsigned nb = (unsigned)((p.M + bs - 1) / bs);
   if (p.stencil == 0) gather_kernel<S, WALLS, 0><<<nb, bs, 0, s>>>(p, a);
   else if (p.stencil == 1) gather_kernel<S, WALLS, 1><<<nb, bs, 0, s>>>(p, a);
   else gather_kernel<S, WALLS, 2><<<nb, bs, 0, s>>>(p, a);
@@ -461,6 +536,35 @@ void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ spreading
+constexpr int MAXNT = 8;    // neighbour tiles per axis in the table
+
+// host: tiles along one axis whose cells overlap [lo - 3, hi + 3] of tile t
+// (markers can sit one cell outside their home tile and their stencils
+// reach two cells beyond their cell)
+void neighbour_tiles(const Geom& g, int maxnt, int* table) {
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const int nt3[3] = {g.ntx, g.nty, g.ntz};
+  for (int d = 0; d < 3; ++d) {
+    const bool periodic = d < 2 || !g.walls;
+    for (int t = 0; t < maxnt; ++t) {
+      int* row = table + (d * maxnt + t) * MAXNT;
+      for (int q = 0; q < MAXNT; ++q) row[q] = -1;
+      if (t >= nt3[d]) continue;
+      const int lo = t * TILE, hi = (lo + TILE < n3[d] ? lo + TILE : n3[d]) - 1;
+      int cnt = 0;
+      for (int c = lo - 3; c <= hi + 3; ++c) {
+        int cc = c;
+        if (periodic) cc = ((c % n3[d]) + n3[d]) % n3[d];
+        else if (c < 0 || c >= n3[d]) continue;
+        const int tn = cc / TILE;
+        bool seen = false;
+        for (int q = 0; q < cnt; ++q) seen = seen || row[q] == tn;
+        if (!seen && cnt < MAXNT) row[cnt++] = tn;
+      }
+    }
+  }
+}
+
 // Distinct cells of one axis that a stencil row b, b+1, ... reaches inside
 // [lo, hi] (after periodic wrap), with the weights of coinciding nodes
 // added.  Returns the count.
@@ -484,25 +588,26 @@ __device__ inline int axis_hits(int b, const C (&w)[4], int n, bool periodic, in
   return cnt;
 }
 
-// tiles (along one axis) that hold markers able to reach cells [lo, hi]:
-// markers are keyed by the cell containing them, and every stencil lies in
-// [cell - 2, cell + 2], so the cells lo - 2 .. hi + 2 are searched
-__device__ inline int axis_tiles(int lo, int hi, int n, bool periodic, int (&out)[8]) {
-  int cnt = 0;
-  for (int c = lo - 2; c <= hi + 2; ++c) {
-    int cc = c;
-    if (periodic) cc = wrap_int(c, n);
-    else if (c < 0 || c >= n) continue;
-    const int t = cc / TILE;
-    bool seen = false;
-    for (int q = 0; q < cnt; ++q) seen |= out[q] == t;
-    if (!seen && cnt < 8) out[cnt++] = t;
-  }
-  return cnt;
+// does the stencil row b .. b + SN - 1 (periodic wrap) meet [lo, hi]?
+template <int SN>
+__device__ inline bool axis_reach(int b, int n, bool periodic, int lo, int hi) {
+  if (!periodic) return b <= hi && b + SN - 1 >= lo;
+  const int off = wrap_int(lo - b, n); // position of lo relative to b, mod n
+  return off < SN || off + (hi - lo) >= n;
 }
 
 // warps per block: 24 KB of shared accumulators either way
 template <typename C> struct SpreadWarps { static constexpr int value = sizeof(C) == 8 ? 2 : 4; };
+
+// one surviving marker, reduced to the cells of the current tile it reaches:
+// per axis the count, local offsets and (folded) weights, plus its force
+template <typename C>
+struct TileHit {
+  int n[3];
+  int loc[3][4];
+  C wt[3][4];
+  C F[3];
+};
 
 template <int ST, typename C>
 __global__ void __launch_bounds__(SpreadWarps<C>::value * 32)
@@ -510,74 +615,123 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   constexpr int SN = nodes_1d<ST>();
   constexpr int WARPS = SpreadWarps<C>::value;
   __shared__ C sacc[WARPS][3][TILE_CELLS];
+  __shared__ TileHit<C> shit[WARPS][32];       // the current round's survivors
   const Geom& g = p.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   C (*acc)[TILE_CELLS] = sacc[wid];
+  TileHit<C>* stage = shit[wid];
   const StencilRecT<C>* recs = static_cast<const StencilRecT<C>*>(a.rec);
   const C* Fin = static_cast<const C*>(a.Fin);
   C* Fout = static_cast<C*>(a.Fout);
   const int ntiles = g.ntx * g.nty * g.ntz;
   const long long nwarps = (long long)gridDim.x * WARPS;
+  const bool perz = !g.walls;
   for (long long tl = (long long)blockIdx.x * WARPS + wid; tl < ntiles; tl += nwarps) {
     const int t = (int)tl;
-    const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
-    const int lo[3] = {tx * TILE, ty * TILE, tz * TILE};
+    const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+    const int lo[3] = {tt[0] * TILE, tt[1] * TILE, tt[2] * TILE};
     const int hi[3] = {min(lo[0] + TILE, g.nx) - 1, min(lo[1] + TILE, g.ny) - 1, min(lo[2] + TILE, g.nz) - 1};
-    int lt[3][8], nt[3];
-    nt[0] = axis_tiles(lo[0], hi[0], g.nx, true, lt[0]);
-    nt[1] = axis_tiles(lo[1], hi[1], g.ny, true, lt[1]);
-    nt[2] = axis_tiles(lo[2], hi[2], g.nz, !g.walls, lt[2]);
-    long long total = 0;
-    for (int qz = 0; qz < nt[2]; ++qz)
-      for (int qy = 0; qy < nt[1]; ++qy)
-        for (int qx = 0; qx < nt[0]; ++qx) {
-          const int tn = (lt[2][qz] * g.nty + lt[1][qy]) * g.ntx + lt[0][qx];
-          total += a.tile_end[tn] - a.tile_begin[tn];
-        }
+    // neighbour tiles per axis: lane q < 8 reads entry q of each table row
+    int rowv[3], nt[3];
+    for (int d = 0; d < 3; ++d) {
+      const int* row = a.ntab + (d * a.maxnt + tt[d]) * MAXNT;
+      rowv[d] = lane < MAXNT ? row[lane] : -1;
+      nt[d] = __popc(__ballot_sync(0xffffffffu, rowv[d] >= 0));
+    }
+    const int ncand = nt[0] * nt[1] * nt[2];
     const bool carry = a.flag_in != nullptr && a.flag_in[t];
-    if (total == 0 && !carry) {
+    bool inited = false;                 // accumulators initialised (warp-uniform)
+    if (carry) {
+      for (int l = lane; l < TILE_CELLS; l += 32) {
+        const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
+        const bool in = x <= hi[0] && y <= hi[1] && z <= hi[2];
+        const long long cell = z * g.plane + (long long)y * g.pitch + x;
+        for (int c = 0; c < 3; ++c) acc[c][l] = in ? Fin[c * g.qstride + cell] : C(0);
+      }
+      __syncwarp();
+      inited = true;
+    }
+    // candidate markers: the ranges of the neighbour tiles, flattened; 32
+    // neighbour tiles per chunk, 32 markers per round
+    for (int qbase = 0; qbase < ncand; qbase += 32) {
+      const int q = qbase + lane;
+      const int qx = q % nt[0], qy = (q / nt[0]) % nt[1], qz = (q / (nt[0] * nt[1])) & (MAXNT - 1);
+      const int tx = __shfl_sync(0xffffffffu, rowv[0], qx);
+      const int ty = __shfl_sync(0xffffffffu, rowv[1], qy);
+      const int tz = __shfl_sync(0xffffffffu, rowv[2], qz);
+      int cnt = 0, kb = 0;
+      if (q < ncand) {
+        const int tn = (tz * g.nty + ty) * g.ntx + tx;
+        kb = a.tile_begin[tn];
+        cnt = a.tile_end[tn] - kb;
+      }
+      int incl = cnt;                    // inclusive prefix of the counts
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      for (int cbase = 0; cbase < total; cbase += 32) {
+        const int cidx = cbase + lane;
+        // owning chunk lane: the first lane whose inclusive prefix exceeds cidx
+        int pos = 0;
+        for (int step = 16; step > 0; step >>= 1) {
+          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+          if (v <= cidx) pos += step;
+        }
+        const int ex = __shfl_sync(0xffffffffu, incl - cnt, pos);
+        const int kq = __shfl_sync(0xffffffffu, kb, pos);
+        const int kk = kq + (cidx - ex);
+        bool hit = false;
+        if (cidx < total) {
+          const short4 r = a.reach[kk];
+          hit = axis_reach<SN>(r.x, g.nx, true, lo[0], hi[0]) &&
+                axis_reach<SN>(r.y, g.ny, true, lo[1], hi[1]) &&
+                axis_reach<SN>(r.z, g.nz, perz, lo[2], hi[2]);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (mask && !inited) {
+          for (int l = lane; l < TILE_CELLS; l += 32)
+            for (int c = 0; c < 3; ++c) acc[c][l] = C(0);
+          inited = true;
+        }
+        // every hit lane reduces its own marker to this tile's cells, all
+        // in parallel; the warp then adds the survivors one after another
+        if (hit) {
+          const StencilRecT<C>& r = recs[kk];
+          TileHit<C>& h = stage[lane];
+          C rw[4];
+          for (int e = 0; e < 4; ++e) rw[e] = r.wx[e];
+          h.n[0] = axis_hits<SN, C>(r.bx, rw, g.nx, true, lo[0], hi[0], h.loc[0], h.wt[0]);
+          for (int e = 0; e < 4; ++e) rw[e] = r.wy[e];
+          h.n[1] = axis_hits<SN, C>(r.by, rw, g.ny, true, lo[1], hi[1], h.loc[1], h.wt[1]);
+          for (int e = 0; e < 4; ++e) rw[e] = r.wz[e];
+          h.n[2] = axis_hits<SN, C>(r.bz, rw, g.nz, perz, lo[2], hi[2], h.loc[2], h.wt[2]);
+          h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
+        }
+        __syncwarp();
+        while (mask) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const TileHit<C>& h = stage[src];
+          const int cxn = h.n[0], cyn = h.n[1], czn = h.n[2];
+          const int items = cxn * cyn * czn;
+          for (int it = lane; it < items; it += 32) {
+            const int ix = it % cxn, iy = (it / cxn) % cyn, iz = it / (cxn * cyn);
+            const int l = (h.loc[2][iz] * TILE + h.loc[1][iy]) * TILE + h.loc[0][ix];
+            const C wt = (h.wt[0][ix] * h.wt[1][iy]) * h.wt[2][iz];
+            acc[0][l] += wt * h.F[0];
+            acc[1][l] += wt * h.F[1];
+            acc[2][l] += wt * h.F[2];
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (!inited) {                       // no marker reaches this tile
       if (lane == 0) a.flag_out[t] = 0;
       continue;
     }
-    for (int l = lane; l < TILE_CELLS; l += 32) {
-      const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
-      const bool in = x <= hi[0] && y <= hi[1] && z <= hi[2];
-      const long long cell = z * g.plane + (long long)y * g.pitch + x;
-      for (int c = 0; c < 3; ++c) acc[c][l] = (carry && in) ? Fin[c * g.qstride + cell] : C(0);
-    }
-    __syncwarp();
-    for (int qz = 0; qz < nt[2]; ++qz)
-      for (int qy = 0; qy < nt[1]; ++qy)
-        for (int qx = 0; qx < nt[0]; ++qx) {
-          const int tn = (lt[2][qz] * g.nty + lt[1][qy]) * g.ntx + lt[0][qx];
-          const int kb = a.tile_begin[tn], ke = a.tile_end[tn];
-          for (int k = kb; k < ke; ++k) {
-            const StencilRecT<C>& r = recs[k];
-            int lx[4], ly[4], lz[4];
-            C wx[4], wy[4], wz[4];
-            C rw[4];
-            for (int q = 0; q < 4; ++q) rw[q] = r.wx[q];
-            const int cxn = axis_hits<SN, C>(r.bx, rw, g.nx, true, lo[0], hi[0], lx, wx);
-            if (cxn == 0) continue;
-            for (int q = 0; q < 4; ++q) rw[q] = r.wy[q];
-            const int cyn = axis_hits<SN, C>(r.by, rw, g.ny, true, lo[1], hi[1], ly, wy);
-            if (cyn == 0) continue;
-            for (int q = 0; q < 4; ++q) rw[q] = r.wz[q];
-            const int czn = axis_hits<SN, C>(r.bz, rw, g.nz, !g.walls, lo[2], hi[2], lz, wz);
-            if (czn == 0) continue;
-            const C F0 = r.F[0], F1 = r.F[1], F2 = r.F[2];
-            const int items = cxn * cyn * czn;
-            for (int it = lane; it < items; it += 32) {
-              const int ix = it % cxn, iy = (it / cxn) % cyn, iz = it / (cxn * cyn);
-              const int l = (lz[iz] * TILE + ly[iy]) * TILE + lx[ix];
-              const C wt = (wx[ix] * wy[iy]) * wz[iz];
-              acc[0][l] += wt * F0;
-              acc[1][l] += wt * F1;
-              acc[2][l] += wt * F2;
-            }
-            __syncwarp();
-          }
-        }
     for (int l = lane; l < TILE_CELLS; l += 32) {
       const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
       if (x <= hi[0] && y <= hi[1] && z <= hi[2]) {
