@@ -62,7 +62,7 @@ struct Layout {
   size_t off_pos[2], off_vel[2], off_fint, off_fh, off_aux, off_mass, off_ext;
   size_t off_key[2], off_idx[2], off_hist, off_tb, off_te, off_rec;
   size_t off_nbr_start, off_nbr_j, off_nbr_k, off_nbr_r0;
-  size_t off_inv_mass, off_reach, off_ntab, off_status;
+  size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
   size_t off_red, off_redout;
   int ntiles, maxnt;
   bool has_particles;
@@ -116,6 +116,9 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.maxnt = g.ntx > g.nty ? (g.ntx > g.ntz ? g.ntx : g.ntz) : (g.nty > g.ntz ? g.nty : g.ntz);
     L.off_ntab = take((size_t)3 * L.maxnt * 8 * sizeof(int));
     L.off_status = take(sizeof(int));
+    L.off_mark = take((size_t)L.ntiles * 4);
+    L.off_live = take((size_t)L.ntiles * 4);
+    L.off_nlive = take(2 * sizeof(int));
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
@@ -320,6 +323,9 @@ struct Plan {
     a.reach = reinterpret_cast<short4*>(b->arena + b->L.off_reach);
     a.keys = b->uptr(b->L.off_key[0]);
     a.status = b->iptr(b->L.off_status);
+    a.mark = reinterpret_cast<uint32_t*>(b->arena + b->L.off_mark);
+    a.live_tiles = b->iptr(b->L.off_live);
+    a.nlive = b->iptr(b->L.off_nlive);
     return a;
   }
 
@@ -342,10 +348,13 @@ struct Plan {
     a.maxnt = b->L.maxnt;
     a.tile_begin = b->iptr(b->L.off_tb);
     a.tile_end = b->iptr(b->L.off_te);
-    a.Fin = carry ? b->F(out) : nullptr;
-    a.flag_in = carry ? b->flag(out) : nullptr;
-    a.Fout = b->F(out);
-    a.flag_out = b->flag(out);
+    a.F = b->F(out);
+    a.flag = b->flag(out);
+    a.accumulate = carry ? 1 : 0;
+    a.mark = reinterpret_cast<uint32_t*>(b->arena + b->L.off_mark);
+    a.live_tiles = b->iptr(b->L.off_live);
+    a.nlive = b->iptr(b->L.off_nlive);
+    a.done = b->iptr(b->L.off_nlive) + 1;
     launch_spread(part_args(b), a, s);
     ++n;
   }
@@ -754,7 +763,9 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
     neighbour_tiles(L.g, L.maxnt, tab.data());
     if (cudaMemcpy(b->iptr(L.off_ntab), tab.data(), tab.size() * sizeof(int),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(b->arena + L.off_mark, 0, (size_t)L.ntiles * 4) != cudaSuccess ||
+        cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess) {
       delete b;
       return LBC_ERR_CUDA;
     }
@@ -925,6 +936,8 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   CK(cudaMemcpyAsync(b->dptr(b->L.off_inv_mass), inv_mass.data(), inv_mass.size() * 8,
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->iptr(b->L.off_status), 0, sizeof(int), s));
+  CK(cudaMemsetAsync(b->arena + b->L.off_mark, 0, (size_t)b->L.ntiles * 4, s));
+  CK(cudaMemsetAsync(b->arena + b->L.off_nlive, 0, 2 * sizeof(int), s));
   CK(cudaMemcpyAsync(b->dptr(b->L.off_ext), ext.data(), ext.size() * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->dptr(b->L.off_fh), 0, 3 * M * 8, s));
   CK(cudaMemsetAsync(b->dptr(b->L.off_fint), 0, 3 * M * 8, s));

@@ -11,7 +11,8 @@
 namespace lbc {
 
 constexpr int Q = 19;
-constexpr int TILE = 8;            // force tiles are TILE^3 cells
+constexpr int TILE_SHIFT = 2;      // force tiles are TILE^3 = 4^3 cells
+constexpr int TILE = 1 << TILE_SHIFT;
 constexpr int TILE_CELLS = TILE * TILE * TILE;
 
 __host__ __device__ constexpr int cx_of(int i) {
@@ -87,7 +88,7 @@ struct Geom {
 };
 
 __host__ __device__ inline int tile_of(const Geom& g, int x, int y, int z) {
-  return (z / TILE * g.nty + y / TILE) * g.ntx + x / TILE;
+  return ((z >> TILE_SHIFT) * g.nty + (y >> TILE_SHIFT)) * g.ntx + (x >> TILE_SHIFT);
 }
 
 // fmod-based wrap into [0, n): the result is r = fmod(X, n), + n if

@@ -135,6 +135,11 @@ struct GatherArgs {
   void* rec;                      // StencilRecT<C>[M], by sorted slot
   short4* reach;                  // stencil base per sorted slot (x, y, z)
   int* status;                    // set to 1 if a marker left its home tile +- 1 cell
+  // tiles a stencil reaches: mark[t] is set once per tile and the tile is
+  // appended to live_tiles[0 .. *nlive) for the spreading that follows
+  uint32_t* mark;
+  int* live_tiles;
+  int* nlive;
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
 
@@ -142,11 +147,15 @@ struct SpreadArgs {
   const void* rec;                            // StencilRecT<C>[M]
   const short4* reach;                        // stencil base per sorted slot
   const int* tile_begin; const int* tile_end;
-  // per axis and tile, the (up to 4) tiles holding markers whose stencil can
-  // reach it: ntab[(axis * maxnt + t) * 4 + q], -1 padded
+  // per axis and tile, the (up to 8) tiles holding markers whose stencil can
+  // reach it: ntab[(axis * maxnt + t) * 8 + q], -1 padded
   const int* ntab; int maxnt;
-  const void* Fin; const uint8_t* flag_in;    // accumulate onto (may be null)
-  void* Fout; uint8_t* flag_out;
+  void* F; uint8_t* flag;         // force field written (or added to) in place
+  int accumulate;                 // 1: add onto the tiles whose flag is set
+  uint32_t* mark;                 // marks of the gather; consumed here
+  const int* live_tiles;          // the marked tiles, in any order
+  int* nlive;                     // their count; reset to 0 on exit
+  int* done;                      // blocks finished (reset to 0 on exit)
 };
 // host: fill the neighbour-tile table (3 * maxnt * 4 ints)
 void neighbour_tiles(const Geom& g, int maxnt, int* table);

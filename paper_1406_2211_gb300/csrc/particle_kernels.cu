@@ -494,6 +494,64 @@ __global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const 
     r.pad = C(0);
     static_cast<StencilRecT<C>*>(a.rec)[k] = r;
     a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+    // claim the tiles the stencil reaches (nodes with non-zero weight); per
+    // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
+    // node's tile or carries no weight
+    int tq[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int t = -1;
+        if (q < SN && w[c][q] != C(0)) {
+          int node = b[c] + q;
+          if (per[c]) node = wrap_int(node, n3[c]);
+          if (node >= 0 && node < n3[c]) t = node >> TILE_SHIFT;
+        }
+#pragma unroll
+        for (int e = 0; e < q; ++e) if (tq[c][e] == t) t = -1;
+        tq[c][q] = t;
+      }
+    }
+    unsigned long long claimed = 0ull;   // bit qz * 16 + qy * 4 + qx
+    int nclaim = 0;
+#pragma unroll
+    for (int qz = 0; qz < 4; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < 4; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < 4; ++qx)
+          if (tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
+            uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
+            if (*m == 0u && atomicExch(m, 1u) == 0u) {
+              claimed |= 1ull << (qz * 16 + qy * 4 + qx);
+              ++nclaim;
+            }
+          }
+    // list slots for the claimed tiles, one atomic per warp; the lanes still
+    // running here are the warp's first nact lanes (slots k < M)
+    const int lane = threadIdx.x & 31;
+    const long long kw = k - lane;
+    const int nact = M - kw >= 32 ? 32 : (int)(M - kw);
+    const unsigned am = nact == 32 ? 0xffffffffu : ((1u << nact) - 1u);
+    int incl = nclaim;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(am, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(am, incl, nact - 1);
+    int base = 0;
+    if (lane == nact - 1 && total > 0) base = atomicAdd(a.nlive, total);
+    base = __shfl_sync(am, base, nact - 1) + incl - nclaim;
+#pragma unroll
+    for (int qz = 0; qz < 4; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < 4; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < 4; ++qx)
+          if (claimed & (1ull << (qz * 16 + qy * 4 + qx)))
+            a.live_tiles[base++] = (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
     if (a.keys) {
       // the bins of this step are valid while the marker stays within one
       // cell of its home tile
@@ -565,29 +623,6 @@ void neighbour_tiles(const Geom& g, int maxnt, int* table) {
   }
 }
 
-// Distinct cells of one axis that a stencil row b, b+1, ... reaches inside
-// [lo, hi] (after periodic wrap), with the weights of coinciding nodes
-// added.  Returns the count.
-template <int SN, typename C>
-__device__ inline int axis_hits(int b, const C (&w)[4], int n, bool periodic, int lo, int hi,
-                                int (&loc)[4], C (&wt)[4]) {
-  int cnt = 0;
-#pragma unroll
-  for (int k = 0; k < SN; ++k) {
-    if (w[k] == C(0)) continue;
-    int c = b + k;
-    if (periodic) c = wrap_int(c, n);
-    else if (c < 0 || c >= n) continue;
-    if (c < lo || c > hi) continue;
-    const int l = c - lo;
-    int found = -1;
-    for (int q = 0; q < cnt; ++q) if (loc[q] == l) found = q;
-    if (found >= 0) wt[found] += w[k];
-    else { loc[cnt] = l; wt[cnt] = w[k]; ++cnt; }
-  }
-  return cnt;
-}
-
 // does the stencil row b .. b + SN - 1 (periodic wrap) meet [lo, hi]?
 template <int SN>
 __device__ inline bool axis_reach(int b, int n, bool periodic, int lo, int hi) {
@@ -596,41 +631,90 @@ __device__ inline bool axis_reach(int b, int n, bool periodic, int lo, int hi) {
   return off < SN || off + (hi - lo) >= n;
 }
 
-// warps per block: 24 KB of shared accumulators either way
-template <typename C> struct SpreadWarps { static constexpr int value = sizeof(C) == 8 ? 2 : 4; };
+// Weights of one stencil row at the TILE cells lo .. lo + TILE - 1 of an
+// axis: nodes b + k (periodic wrap, or dropped outside the box) that land on
+// the same cell have their weights added in k order.
+template <int SN, typename C>
+__device__ inline void tile_weights(int b, const C (&w)[4], int n, bool periodic, int lo,
+                                    C (&out)[TILE]) {
+  int node[SN];
+#pragma unroll
+  for (int k = 0; k < SN; ++k) {
+    int c = b + k;
+    if (periodic) c = wrap_int(c, n);
+    else if (c < 0 || c >= n) c = -1;
+    node[k] = w[k] == C(0) ? -1 : c - lo;
+  }
+#pragma unroll
+  for (int j = 0; j < TILE; ++j) {
+    C acc = C(0);
+#pragma unroll
+    for (int k = 0; k < SN; ++k) acc += node[k] == j ? w[k] : C(0);
+    out[j] = acc;
+  }
+}
 
-// one surviving marker, reduced to the cells of the current tile it reaches:
-// per axis the count, local offsets and (folded) weights, plus its force
+// a surviving marker reduced to the current tile: per axis the weights at
+// the tile's TILE cells, and its force
 template <typename C>
-struct TileHit {
-  int n[3];
-  int loc[3][4];
-  C wt[3][4];
+struct SpreadHit {
+  C w[3][TILE];
   C F[3];
+  C pad;
 };
 
+constexpr int SPREAD_THREADS = 256;
+
+// Spreading, one warp per live tile (a tile some stencil reaches), taken from
+// the list the gather built.  Lane l owns the cells (l & 3, (l >> 2) & 3,
+// l >> 4) and the same cell two planes up, and keeps their force sums in
+// registers.  The candidates are the markers binned in the neighbour tiles;
+// 32 of them are tested at a time, each surviving lane reduces its own
+// marker to the tile, and the warp then adds the survivors in candidate
+// order, so the sums are formed in a fixed order (no atomics).
 template <int ST, typename C>
-__global__ void __launch_bounds__(SpreadWarps<C>::value * 32)
+__global__ void __launch_bounds__(SPREAD_THREADS, 4)
 spread_kernel(const PartArgs p, const SpreadArgs a) {
+  static_assert(TILE == 4 && TILE_CELLS == 64, "two cells per lane");
   constexpr int SN = nodes_1d<ST>();
-  constexpr int WARPS = SpreadWarps<C>::value;
-  __shared__ C sacc[WARPS][3][TILE_CELLS];
-  __shared__ TileHit<C> shit[WARPS][32];       // the current round's survivors
+  constexpr int WARPS = SPREAD_THREADS / 32;
+  __shared__ SpreadHit<C> shit[WARPS][32];
+  __shared__ int s_nlive;
   const Geom& g = p.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  C (*acc)[TILE_CELLS] = sacc[wid];
-  TileHit<C>* stage = shit[wid];
+  SpreadHit<C>* stage = shit[wid];
   const StencilRecT<C>* recs = static_cast<const StencilRecT<C>*>(a.rec);
-  const C* Fin = static_cast<const C*>(a.Fin);
-  C* Fout = static_cast<C*>(a.Fout);
+  C* F = static_cast<C*>(a.F);
   const int ntiles = g.ntx * g.nty * g.ntz;
-  const long long nwarps = (long long)gridDim.x * WARPS;
   const bool perz = !g.walls;
-  for (long long tl = (long long)blockIdx.x * WARPS + wid; tl < ntiles; tl += nwarps) {
-    const int t = (int)tl;
+  if (threadIdx.x == 0) s_nlive = *a.nlive;
+  // tiles no stencil reaches keep their flag when accumulating and are
+  // cleared otherwise; the marks are consumed
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (a.mark[t] != 0u) a.mark[t] = 0u;
+    else if (!a.accumulate) a.flag[t] = 0;
+  }
+  __syncthreads();
+  const int nlive = s_nlive;
+  const int cxl = lane & 3, cyl = (lane >> 2) & 3, czl = lane >> 4;
+  for (int j = blockIdx.x * WARPS + wid; j < nlive; j += gridDim.x * WARPS) {
+    const int t = a.live_tiles[j];
     const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
     const int lo[3] = {tt[0] * TILE, tt[1] * TILE, tt[2] * TILE};
     const int hi[3] = {min(lo[0] + TILE, g.nx) - 1, min(lo[1] + TILE, g.ny) - 1, min(lo[2] + TILE, g.nz) - 1};
+    const int x = lo[0] + cxl, y = lo[1] + cyl, z0 = lo[2] + czl, z1 = z0 + 2;
+    const bool in0 = x <= hi[0] && y <= hi[1] && z0 <= hi[2];
+    const bool in1 = x <= hi[0] && y <= hi[1] && z1 <= hi[2];
+    const long long cell0 = z0 * g.plane + (long long)y * g.pitch + x;
+    const long long cell1 = cell0 + 2 * g.plane;
+    C acc0[3] = {C(0), C(0), C(0)}, acc1[3] = {C(0), C(0), C(0)};
+    if (a.accumulate && a.flag[t]) {
+      for (int c = 0; c < 3; ++c) {
+        if (in0) acc0[c] = F[c * g.qstride + cell0];
+        if (in1) acc1[c] = F[c * g.qstride + cell1];
+      }
+    }
     // neighbour tiles per axis: lane q < 8 reads entry q of each table row
     int rowv[3], nt[3];
     for (int d = 0; d < 3; ++d) {
@@ -639,18 +723,6 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
       nt[d] = __popc(__ballot_sync(0xffffffffu, rowv[d] >= 0));
     }
     const int ncand = nt[0] * nt[1] * nt[2];
-    const bool carry = a.flag_in != nullptr && a.flag_in[t];
-    bool inited = false;                 // accumulators initialised (warp-uniform)
-    if (carry) {
-      for (int l = lane; l < TILE_CELLS; l += 32) {
-        const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
-        const bool in = x <= hi[0] && y <= hi[1] && z <= hi[2];
-        const long long cell = z * g.plane + (long long)y * g.pitch + x;
-        for (int c = 0; c < 3; ++c) acc[c][l] = in ? Fin[c * g.qstride + cell] : C(0);
-      }
-      __syncwarp();
-      inited = true;
-    }
     // candidate markers: the ranges of the neighbour tiles, flattened; 32
     // neighbour tiles per chunk, 32 markers per round
     for (int qbase = 0; qbase < ncand; qbase += 32) {
@@ -690,77 +762,69 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
                 axis_reach<SN>(r.z, g.nz, perz, lo[2], hi[2]);
         }
         unsigned mask = __ballot_sync(0xffffffffu, hit);
-        if (mask && !inited) {
-          for (int l = lane; l < TILE_CELLS; l += 32)
-            for (int c = 0; c < 3; ++c) acc[c][l] = C(0);
-          inited = true;
-        }
-        // every hit lane reduces its own marker to this tile's cells, all
-        // in parallel; the warp then adds the survivors one after another
         if (hit) {
           const StencilRecT<C>& r = recs[kk];
-          TileHit<C>& h = stage[lane];
+          SpreadHit<C>& h = stage[lane];
           C rw[4];
           for (int e = 0; e < 4; ++e) rw[e] = r.wx[e];
-          h.n[0] = axis_hits<SN, C>(r.bx, rw, g.nx, true, lo[0], hi[0], h.loc[0], h.wt[0]);
+          tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
           for (int e = 0; e < 4; ++e) rw[e] = r.wy[e];
-          h.n[1] = axis_hits<SN, C>(r.by, rw, g.ny, true, lo[1], hi[1], h.loc[1], h.wt[1]);
+          tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
           for (int e = 0; e < 4; ++e) rw[e] = r.wz[e];
-          h.n[2] = axis_hits<SN, C>(r.bz, rw, g.nz, perz, lo[2], hi[2], h.loc[2], h.wt[2]);
+          tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
           h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
         }
         __syncwarp();
         while (mask) {
           const int src = __ffs(mask) - 1;
           mask &= mask - 1;
-          const TileHit<C>& h = stage[src];
-          const int cxn = h.n[0], cyn = h.n[1], czn = h.n[2];
-          const int items = cxn * cyn * czn;
-          for (int it = lane; it < items; it += 32) {
-            const int ix = it % cxn, iy = (it / cxn) % cyn, iz = it / (cxn * cyn);
-            const int l = (h.loc[2][iz] * TILE + h.loc[1][iy]) * TILE + h.loc[0][ix];
-            const C wt = (h.wt[0][ix] * h.wt[1][iy]) * h.wt[2][iz];
-            acc[0][l] += wt * h.F[0];
-            acc[1][l] += wt * h.F[1];
-            acc[2][l] += wt * h.F[2];
-          }
-          __syncwarp();
+          const SpreadHit<C>& h = stage[src];
+          const C wxy = h.w[0][cxl] * h.w[1][cyl];
+          const C w0 = wxy * h.w[2][czl], w1 = wxy * h.w[2][czl + 2];
+          const C f0 = h.F[0], f1 = h.F[1], f2 = h.F[2];
+          acc0[0] += w0 * f0; acc0[1] += w0 * f1; acc0[2] += w0 * f2;
+          acc1[0] += w1 * f0; acc1[1] += w1 * f1; acc1[2] += w1 * f2;
         }
+        __syncwarp();
       }
     }
-    if (!inited) {                       // no marker reaches this tile
-      if (lane == 0) a.flag_out[t] = 0;
-      continue;
+    for (int c = 0; c < 3; ++c) {
+      if (in0) F[c * g.qstride + cell0] = acc0[c];
+      if (in1) F[c * g.qstride + cell1] = acc1[c];
     }
-    for (int l = lane; l < TILE_CELLS; l += 32) {
-      const int x = lo[0] + (l & 7), y = lo[1] + ((l >> 3) & 7), z = lo[2] + (l >> 6);
-      if (x <= hi[0] && y <= hi[1] && z <= hi[2]) {
-        const long long cell = z * g.plane + (long long)y * g.pitch + x;
-        for (int c = 0; c < 3; ++c) Fout[c * g.qstride + cell] = acc[c][l];
-      }
-    }
-    if (lane == 0) a.flag_out[t] = 1;
-    __syncwarp();
+    if (lane == 0) a.flag[t] = 1;
   }
+  // the last block to finish resets the list for the next gather (every
+  // block read the count before it got here)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.done, 1) == (int)gridDim.x - 1) {
+      *a.nlive = 0;
+      *a.done = 0;
+    }
+  }
+}
+
+template <int ST, typename C>
+static void spread_launch(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
+  // a persistent grid: as many blocks as fit on the device at once
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spread_kernel<ST, C>, SPREAD_THREADS, 0);
+    grid = (sms > 0 ? sms : 148) * (per > 0 ? per : 1);
+  }
+  spread_kernel<ST, C><<<grid, SPREAD_THREADS, 0, s>>>(p, a);
 }
 
 template <typename C>
 static void spread_c(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
-  constexpr int WARPS = SpreadWarps<C>::value;
-  const int ntiles = p.g.ntx * p.g.nty * p.g.ntz;
-  static int sms = 0;              // SM count of the first device used
-  if (sms == 0) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    sms = v > 0 ? v : 148;
-  }
-  long long want = (ntiles + WARPS - 1) / WARPS;
-  long long cap = (long long)sms * 48 / WARPS;
-  const unsigned nb = (unsigned)(want < cap ? want : cap);
-  if (p.stencil == 0) spread_kernel<0, C><<<nb, WARPS * 32, 0, s>>>(p, a);
-  else if (p.stencil == 1) spread_kernel<1, C><<<nb, WARPS * 32, 0, s>>>(p, a);
-  else spread_kernel<2, C><<<nb, WARPS * 32, 0, s>>>(p, a);
+  if (p.stencil == 0) spread_launch<0, C>(p, a, s);
+  else if (p.stencil == 1) spread_launch<1, C>(p, a, s);
+  else spread_launch<2, C>(p, a, s);
 }
 
 void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
