@@ -61,11 +61,13 @@ struct Layout {
   size_t off_pop[2], off_F[2], off_flag[2];
   size_t off_pos[2], off_vel[2], off_fint, off_fh, off_aux, off_mass, off_ext;
   size_t off_key[2], off_idx[2], off_hist, off_tb, off_te, off_rec;
-  size_t off_nbr_start, off_nbr_j, off_nbr_k, off_nbr_r0;
+  size_t off_nbr_start, off_nbr_j, off_nbr_kr, off_nbr_r0sq;
   size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
+  size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
   size_t off_red, off_redout;
   int ntiles, maxnt;
   bool has_particles;
+  bool use_ncache;
 };
 
 Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_t M, int64_t B) {
@@ -95,9 +97,10 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     const size_t v3 = 3 * (size_t)M * sizeof(double);
     L.off_pos[0] = take(v3); L.off_pos[1] = take(v3);
     L.off_vel[0] = take(v3); L.off_vel[1] = take(v3);
-    L.off_fint = take(v3); L.off_fh = take(v3); L.off_aux = take(v3);
+    const size_t c3 = 3 * (size_t)M * force_elem_bytes(l->storage);   // [3][M] compute type
+    L.off_fint = take(c3); L.off_fh = take(v3); L.off_aux = take(v3);
     L.off_mass = take((size_t)M * sizeof(double));
-    L.off_ext = take(v3);
+    L.off_ext = take(c3);
     for (int k = 0; k < 2; ++k) {
       L.off_key[k] = take((size_t)M * 4);
       L.off_idx[k] = take((size_t)M * 4);
@@ -109,16 +112,23 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_nbr_start = take((size_t)(M + 1) * 4);
     const size_t nb2 = (size_t)(2 * B > 0 ? 2 * B : 1);
     L.off_nbr_j = take(nb2 * 4);
-    L.off_nbr_k = take(nb2 * 8);
-    L.off_nbr_r0 = take(nb2 * 8);
+    L.off_nbr_kr = take(nb2 * 2 * force_elem_bytes(l->storage));
+    L.off_nbr_r0sq = take(nb2 * 8);
     L.off_inv_mass = take((size_t)M * sizeof(double));
     L.off_reach = take((size_t)M * sizeof(short4));
     L.maxnt = g.ntx > g.nty ? (g.ntx > g.ntz ? g.ntx : g.ntz) : (g.nty > g.ntz ? g.nty : g.ntz);
     L.off_ntab = take((size_t)3 * L.maxnt * 8 * sizeof(int));
     L.off_status = take(sizeof(int));
     L.off_mark = take((size_t)L.ntiles * 4);
-    L.off_live = take((size_t)L.ntiles * 4);
+    L.off_live = take((size_t)L.ntiles * 16);
     L.off_nlive = take(2 * sizeof(int));
+    // the coupled sub-steps of the multistep split reuse the node moments
+    const bool multistep = c->kind != LBC_IBM && c->order == 2 && c->split == LBC_SPLIT_INSIDE &&
+                           c->substeps > 1;
+    const int sn = c->stencil == LBC_TRILINEAR ? 2 : (c->stencil == LBC_PESKIN4 ? 4 : 3);
+    L.off_ncache = take(multistep ? (size_t)sn * sn * sn * 4 * M * force_elem_bytes(l->storage) : 0);
+    L.off_ncache_b = take(multistep ? (size_t)M * 16 : 0);
+    L.use_ncache = multistep;
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
@@ -270,15 +280,15 @@ struct Plan {
     d.vel_in = b->dptr(b->L.off_vel[b->pc]);
     d.pos_out = write ? b->dptr(b->L.off_pos[1 - b->pc]) : nullptr;
     d.vel_out = write ? b->dptr(b->L.off_vel[1 - b->pc]) : nullptr;
-    d.fint_out = force ? b->dptr(b->L.off_fint) : nullptr;
+    d.fint_out = force ? static_cast<void*>(b->arena + b->L.off_fint) : nullptr;
     d.key_out = b->uptr(b->L.off_key[0]);
     d.idx_out = b->uptr(b->L.off_idx[0]);
     d.inv_mass = b->dptr(b->L.off_inv_mass);
-    d.ext = b->dptr(b->L.off_ext);
+    d.ext = b->arena + b->L.off_ext;
     d.nbr_start = b->iptr(b->L.off_nbr_start);
     d.nbr_j = b->iptr(b->L.off_nbr_j);
-    d.nbr_k = b->dptr(b->L.off_nbr_k);
-    d.nbr_r0 = b->dptr(b->L.off_nbr_r0);
+    d.nbr_kr = b->arena + b->L.off_nbr_kr;
+    d.nbr_r0sq = b->dptr(b->L.off_nbr_r0sq);
     launch_drift(part_args(b), d, s);
     if (write) b->pc = 1 - b->pc;
     if (key) b->sorted = false;
@@ -316,7 +326,7 @@ struct Plan {
     a.pos = b->dptr(b->L.off_pos[b->pc]);
     a.vel = b->dptr(b->L.off_vel[b->pc]);
     a.aux = b->dptr(b->L.off_aux);
-    a.fint = b->dptr(b->L.off_fint);
+    a.fint = b->arena + b->L.off_fint;
     a.inv_mass = b->dptr(b->L.off_inv_mass);
     a.fh_out = b->dptr(b->L.off_fh);
     a.rec = b->arena + b->L.off_rec;
@@ -324,8 +334,10 @@ struct Plan {
     a.keys = b->uptr(b->L.off_key[0]);
     a.status = b->iptr(b->L.off_status);
     a.mark = reinterpret_cast<uint32_t*>(b->arena + b->L.off_mark);
-    a.live_tiles = b->iptr(b->L.off_live);
+    a.live_tiles = reinterpret_cast<int4*>(b->arena + b->L.off_live);
     a.nlive = b->iptr(b->L.off_nlive);
+    a.ncache = b->arena + b->L.off_ncache;
+    a.ncache_b = reinterpret_cast<int4*>(b->arena + b->L.off_ncache_b);
     return a;
   }
 
@@ -352,7 +364,7 @@ struct Plan {
     a.flag = b->flag(out);
     a.accumulate = carry ? 1 : 0;
     a.mark = reinterpret_cast<uint32_t*>(b->arena + b->L.off_mark);
-    a.live_tiles = b->iptr(b->L.off_live);
+    a.live_tiles = reinterpret_cast<int4*>(b->arena + b->L.off_live);
     a.nlive = b->iptr(b->L.off_nlive);
     a.done = b->iptr(b->L.off_nlive) + 1;
     launch_spread(part_args(b), a, s);
@@ -466,11 +478,14 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
         }
         GatherArgs a = P.gather_base();
         a.mode = GM_COUPLE; a.s = dt; a.include_int = 1; a.rec_weight = 1.0 / n;
+        // the populations and the fixed field are the same for the n
+        // sub-steps of a half: node moments are stored at the first one
+        if (b->L.use_ncache) a.cache = k == 0 ? 1 : 2;
         const double gfrac = 0.5 * h * double(k) / n;
         if (half == 0)
           P.fields(a, ia, 0.5 * h, k > 0 ? ib : -1, 0.5 * h, 0.5 * h + gfrac);
         else
-          P.fields(a, k > 0 ? ia : -1, 0.5 * h, -1, 0.0, gfrac);
+          P.fields(a, -1, 0.0, k > 0 ? ia : -1, 0.5 * h, gfrac);
         P.gather(a);
         P.spread(out, k > 0);
       }
@@ -938,13 +953,29 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   CK(cudaMemsetAsync(b->iptr(b->L.off_status), 0, sizeof(int), s));
   CK(cudaMemsetAsync(b->arena + b->L.off_mark, 0, (size_t)b->L.ntiles * 4, s));
   CK(cudaMemsetAsync(b->arena + b->L.off_nlive, 0, 2 * sizeof(int), s));
-  CK(cudaMemcpyAsync(b->dptr(b->L.off_ext), ext.data(), ext.size() * 8, cudaMemcpyHostToDevice, s));
+  // external forces, bond constants and rest lengths in the compute type
+  // (the same roundings the kernels would apply), r0^2 in FP64
+  const bool f64 = b->lat.storage == LBC_F64;
+  const size_t ce = f64 ? 8 : 4;
+  std::vector<unsigned char> ext_c(ext.size() * ce), kr_c(2 * nj.size() * ce);
+  std::vector<double> r0sq(nj.size());
+  auto put = [&](std::vector<unsigned char>& dst, size_t at, double v) {
+    if (f64) std::memcpy(dst.data() + at * 8, &v, 8);
+    else { const float f = (float)v; std::memcpy(dst.data() + at * 4, &f, 4); }
+  };
+  for (size_t q = 0; q < ext.size(); ++q) put(ext_c, q, ext[q]);
+  for (size_t q = 0; q < nj.size(); ++q) {
+    put(kr_c, 2 * q, nk[q]);
+    put(kr_c, 2 * q + 1, nr[q]);
+    r0sq[q] = nr[q] * nr[q];
+  }
+  CK(cudaMemcpyAsync(b->arena + b->L.off_ext, ext_c.data(), ext_c.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->dptr(b->L.off_fh), 0, 3 * M * 8, s));
-  CK(cudaMemsetAsync(b->dptr(b->L.off_fint), 0, 3 * M * 8, s));
+  CK(cudaMemsetAsync(b->arena + b->L.off_fint, 0, 3 * M * ce, s));
   CK(cudaMemcpyAsync(b->iptr(b->L.off_nbr_start), start.data(), start.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->iptr(b->L.off_nbr_j), nj.data(), nj.size() * 4, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(b->dptr(b->L.off_nbr_k), nk.data(), nk.size() * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(b->dptr(b->L.off_nbr_r0), nr.data(), nr.size() * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b->arena + b->L.off_nbr_kr, kr_c.data(), kr_c.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b->dptr(b->L.off_nbr_r0sq), r0sq.data(), r0sq.size() * 8, cudaMemcpyHostToDevice, s));
   b->sorted = false;
   reset_graphs(b);
   CK(cudaStreamSynchronize(s));

@@ -59,7 +59,7 @@ void launch_invariants(int storage, const void* fstar, const LBArgs& a,
 // one marker's stencil in sorted order; C is the compute type of the
 // storage (80 bytes for float, 144 for double)
 template <typename C>
-struct StencilRecT {
+struct alignas(16) StencilRecT {
   int bx, by, bz, kind;      // base node per axis; stencil kind
   C wx[4], wy[4], wz[4];     // 1-D weights of the nodes base + k
   C F[3];                    // force to spread (already signed and weighted)
@@ -89,11 +89,12 @@ struct DriftArgs {
   int write_key;         // tile key of the final positions
   const double* pos_in; const double* vel_in;   // [3][M]
   double* pos_out; double* vel_out;             // may alias nothing
-  double* fint_out;                              // [3][M] or null
+  void* fint_out;                                // [3][M] compute type, or null
   uint32_t* key_out; uint32_t* idx_out;
-  const double* inv_mass; const double* ext;    // ext [3][M]
-  const int* nbr_start; const int* nbr_j;
-  const double* nbr_k; const double* nbr_r0;
+  const double* inv_mass; const void* ext;      // ext [3][M] compute type
+  const int* nbr_start; const int* nbr_j;       // bonds per particle (CSR)
+  const void* nbr_kr;                            // (k, r0) per entry, compute type
+  const double* nbr_r0sq;                        // r0^2 per entry
 };
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
 
@@ -121,16 +122,24 @@ struct GatherArgs {
   double s;             // step of this force / position update
   double gamma, rho0;
   double rec_weight;    // spread force = rec_weight * (-F^h) (or +F_int)
-  // fluid velocity (j + c1 F1 + c2 F2 + cg g) / rho at the stencil nodes
+  // fluid velocity (((j + c1 F1) + cg g) + c2 F2) / rho at the stencil
+  // nodes; F1 stays fixed over the sub-steps of a half step, F2 is the field
+  // being accumulated by them
   const void* pops; int storage; float scale16;
   double bb_bot[Q]; double bb_top[Q];
   const void* F1; const uint8_t* flag1; double c1;
   const void* F2; const uint8_t* flag2; double c2;
   double cg; double gvec[3]; double rho0_pop;
+  // per-slot cache of j + c1 F1 and 1 / rho at the stencil nodes, valid
+  // while pops and F1 are unchanged: 0 unused, 1 store, 2 reuse where the
+  // slot's stencil base is the stored one.  Layout [(node * 4 + c) * M + k];
+  // ncache_b[k] holds the base it was taken at.
+  int cache; void* ncache; int4* ncache_b;
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
   const uint32_t* keys;           // sorted home tile of each slot (null: no check)
-  double* pos; double* aux; double* vel; const double* fint;
+  double* pos; double* aux; double* vel;
+  const void* fint;               // [3][M] intrinsic forces, compute type
   const double* inv_mass; double* fh_out;
   void* rec;                      // StencilRecT<C>[M], by sorted slot
   short4* reach;                  // stencil base per sorted slot (x, y, z)
@@ -138,7 +147,7 @@ struct GatherArgs {
   // tiles a stencil reaches: mark[t] is set once per tile and the tile is
   // appended to live_tiles[0 .. *nlive) for the spreading that follows
   uint32_t* mark;
-  int* live_tiles;
+  int4* live_tiles;               // (tile, tx, ty, tz)
   int* nlive;
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
@@ -153,7 +162,7 @@ struct SpreadArgs {
   void* F; uint8_t* flag;         // force field written (or added to) in place
   int accumulate;                 // 1: add onto the tiles whose flag is set
   uint32_t* mark;                 // marks of the gather; consumed here
-  const int* live_tiles;          // the marked tiles, in any order
+  const int4* live_tiles;         // the marked tiles (t, tx, ty, tz), in any order
   int* nlive;                     // their count; reset to 0 on exit
   int* done;                      // blocks finished (reset to 0 on exit)
 };

@@ -127,30 +127,48 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
   }
   C F[3] = {C(0), C(0), C(0)};
   if (d.compute_force) {
-    for (int c = 0; c < 3; ++c) F[c] = (C)d.ext[c * M + i];
+    const C* ext = static_cast<const C*>(d.ext);
+    const C* kr = static_cast<const C*>(d.nbr_kr);
+    for (int c = 0; c < 3; ++c) F[c] = ext[c * M + i];
     const int bbeg = d.nbr_start[i], bend = d.nbr_start[i + 1];
     for (int b = bbeg; b < bend; ++b) {
       const long long j = d.nbr_j[b];
       double e[3];
+      C ec[3];
       double dist2 = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double vj = d.vel_in[c * M + j];
         const double rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
-        e[c] = min_image(rj - r1[c], n3[c], per[c]);
+        e[c] = rj - r1[c];
+        if (sizeof(C) == 4 && per[c]) {
+          // minimum image: the FP32 copy decides unless it lies within
+          // rounding of n/2, where the FP64 test is taken
+          float ef = (float)e[c];
+          if (fabsf(ef) >= 0.4999f * n3[c]) {
+            e[c] = min_image(e[c], n3[c], true);
+            ef = (float)e[c];
+          }
+          ec[c] = (C)ef;
+        } else {
+          e[c] = min_image(e[c], n3[c], per[c]);
+          ec[c] = (C)e[c];
+        }
         dist2 += e[c] * e[c];
       }
       // stretch |d| - r0 = (|d|^2 - r0^2) / (|d| + r0): the difference of
       // squares in FP64 (bonds sit near their rest length, where |d| - r0
       // formed in FP32 would lose most of its digits), the rest in C
-      const double r0 = d.nbr_r0[b];
+      const C k = kr[2 * b], r0 = kr[2 * b + 1];
       const C dist = sqrt((C)dist2);
-      const C stretch = (C)(dist2 - r0 * r0) / (dist + (C)r0);
-      const C mag = C(d.nbr_k[b]) * stretch / dist;
-      for (int c = 0; c < 3; ++c) F[c] += (C)e[c] * mag;
+      const C stretch = (C)(dist2 - d.nbr_r0sq[b]) / (dist + r0);
+      const C mag = k * stretch / dist;
+      for (int c = 0; c < 3; ++c) F[c] += ec[c] * mag;
     }
-    if (d.fint_out)
-      for (int c = 0; c < 3; ++c) d.fint_out[c * M + i] = (double)F[c];
+    if (d.fint_out) {
+      C* fo = static_cast<C*>(d.fint_out);
+      for (int c = 0; c < 3; ++c) fo[c * M + i] = F[c];
+    }
   }
   const double kick = d.dt_kick * d.inv_mass[i];
   double r2[3];
@@ -329,9 +347,10 @@ void launch_tile_ranges(int ntiles, long long M, const uint32_t* keys, int* tb, 
 }
 
 // ------------------------------------------------------------ gather + couple
+// j + c1 F1 (F1 where its tile flag is set) and 1 / rho at node (x, y, z)
 template <typename S, bool WALLS>
-__device__ inline void node_velocity(const GatherArgs& a, const Geom& g, int x, int y, int z,
-                                     typename Store<S>::C (&u)[3]) {
+__device__ inline void node_base(const GatherArgs& a, const Geom& g, int x, int y, int z,
+                                 typename Store<S>::C (&j)[3], typename Store<S>::C& inv) {
   using C = typename Store<S>::C;
   C f[Q];
   pull_cell<S, WALLS>(static_cast<const S*>(a.pops), g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
@@ -344,23 +363,14 @@ __device__ inline void node_velocity(const GatherArgs& a, const Geom& g, int x, 
     if (cy_of(i)) j1 += C(cy_of(i)) * v;
     if (cz_of(i)) j2 += C(cz_of(i)) * v;
   }
-  const long long cell = z * g.plane + (long long)y * g.pitch + x;
-  const int t = tile_of(g, x, y, z);
-  j0 += C(a.cg * a.gvec[0]);
-  j1 += C(a.cg * a.gvec[1]);
-  j2 += C(a.cg * a.gvec[2]);
   const C* F1 = static_cast<const C*>(a.F1);
-  const C* F2 = static_cast<const C*>(a.F2);
-  if (F1 && a.flag1[t]) {
+  if (F1 && a.flag1[tile_of(g, x, y, z)]) {
+    const long long cell = z * g.plane + (long long)y * g.pitch + x;
     const C c1 = C(a.c1);
     j0 += c1 * F1[cell]; j1 += c1 * F1[g.qstride + cell]; j2 += c1 * F1[2 * g.qstride + cell];
   }
-  if (F2 && a.flag2[t]) {
-    const C c2 = C(a.c2);
-    j0 += c2 * F2[cell]; j1 += c2 * F2[g.qstride + cell]; j2 += c2 * F2[2 * g.qstride + cell];
-  }
-  const C inv = C(1) / (C(a.rho0_pop) + rd);
-  u[0] = j0 * inv; u[1] = j1 * inv; u[2] = j2 * inv;
+  j[0] = j0; j[1] = j1; j[2] = j2;
+  inv = C(1) / (C(a.rho0_pop) + rd);
 }
 
 // is cell c within [lo - 1, hi + 1] of its home tile (periodic wrap)?
@@ -373,16 +383,71 @@ __device__ inline bool near_home(int c, int lo, int hi, int n, bool periodic) {
   return d >= -1 && d <= hi - lo + 1;
 }
 
-// One marker per lane (sorted slot k): the position is turned into a
-// stencil base and fraction, the lane walks the stencil nodes itself (their
-// loads are independent, so many are in flight per warp) and then does the
-// FP64 coupling update of its own marker.
-template <typename S, bool WALLS, int ST>
-__global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const GatherArgs a) {
+// Gather and coupling update, one marker (sorted slot k) per thread.  The
+// work of a thread is a chain of dependent memory accesses (slot, particle,
+// stencil, node data, force tile, claims), so what does not depend on the
+// chain is issued with it: the particle's own data is read before the node
+// loop, the eight trilinear nodes are unrolled (their loads are in flight
+// together), and a tile is claimed with one atomic exchange.
+constexpr int GATHER_THREADS = 128;
+
+// one cached node: j (3) and 1 / rho, stored as one 16-byte (float) or two
+// 16-byte (double) vectors
+__device__ inline void cache_load(const float* p, float (&j)[3], float& inv) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  j[0] = v.x; j[1] = v.y; j[2] = v.z; inv = v.w;
+}
+__device__ inline void cache_load(const double* p, double (&j)[3], double& inv) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  j[0] = v0.x; j[1] = v0.y; j[2] = v1.x; inv = v1.y;
+}
+__device__ inline void cache_store(float* p, const float (&j)[3], float inv) {
+  *reinterpret_cast<float4*>(p) = make_float4(j[0], j[1], j[2], inv);
+}
+__device__ inline void cache_store(double* p, const double (&j)[3], double inv) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(j[0], j[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(j[2], inv);
+}
+
+// fluid velocity at one stencil node (x, y, z) of weight wt, added to own:
+// ((j + c1 F1) + cg g + c2 F2) / rho, with j + c1 F1 and 1 / rho taken from
+// the node cache where it is valid
+template <typename S, bool WALLS>
+__device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, int x, int y, int z,
+                                            typename Store<S>::C wt, bool reuse,
+                                            typename Store<S>::C* slot,
+                                            const typename Store<S>::C (&cgg)[3],
+                                            typename Store<S>::C (&own)[3]) {
+  using C = typename Store<S>::C;
+  C j[3], inv;
+  if (reuse) {
+    cache_load(slot, j, inv);
+  } else {
+    node_base<S, WALLS>(a, g, x, y, z, j, inv);
+    if (a.cache != 0) cache_store(slot, j, inv);
+  }
+  j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
+  const C* F2 = static_cast<const C*>(a.F2);
+  if (F2 && a.flag2[tile_of(g, x, y, z)]) {
+    const long long cell = z * g.plane + (long long)y * g.pitch + x;
+    const C c2 = C(a.c2);
+    j[0] += c2 * F2[cell]; j[1] += c2 * F2[g.qstride + cell]; j[2] += c2 * F2[2 * g.qstride + cell];
+  }
+  own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
+}
+
+// REUSE: launched for sub-steps that read the node cache (fewer registers,
+// more markers in flight); the others keep registers for the population
+// loads of two nodes at a time
+template <typename S, bool WALLS, int ST, bool REUSE>
+__global__ void __launch_bounds__(GATHER_THREADS, (REUSE && sizeof(typename Store<S>::C) == 4) ? 6 : 4)
+gather_kernel(const PartArgs p, const GatherArgs a) {
   using C = typename Store<S>::C;
   constexpr int SN = nodes_1d<ST>();
   const Geom& g = p.g;
   const long long M = p.M;
+  const int lane = threadIdx.x & 31;
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool active = k < M;
   if (!active) return;
@@ -390,11 +455,30 @@ __global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const 
   const int n3[3] = {g.nx, g.ny, g.nz};
   const bool per[3] = {true, true, !g.walls};
 
+  // the particle's own data (independent of the gather)
+  double v[3] = {0.0, 0.0, 0.0};
+  double im = 0.0;
+  C Fi[3] = {C(0), C(0), C(0)};
+  const C* fint = static_cast<const C*>(a.fint);
+  if (a.mode == GM_COUPLE) {
+    im = a.inv_mass[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = a.vel[c * M + i];
+      if (a.include_int) Fi[c] = fint[c * M + i];
+    }
+  } else if (a.mode == GM_IBM_HALF || a.mode == GM_IBM1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Fi[c] = fint[c * M + i];
+  }
+  const int home = a.keys ? (int)a.keys[k] : 0;
+
   const bool at_aux = a.mode == GM_IBM_HALF || a.mode == GM_IBM_FINAL;
   const double* P = at_aux ? a.aux : a.pos;
   int b[3];
   C w[3][4];
   double X[3];
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
     X[c] = P[c * M + i];
     stencil_1d<ST, C>(X[c], b[c], w[c]);
@@ -402,47 +486,60 @@ __global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const 
 
   C own[3] = {C(0), C(0), C(0)};
   if (a.mode != GM_IBM1) {
-    int xs[SN], ys[SN];
+    int xs[SN], ys[SN], zs[SN];
 #pragma unroll
     for (int q = 0; q < SN; ++q) {
       xs[q] = wrap_int(b[0] + q, g.nx);
       ys[q] = wrap_int(b[1] + q, g.ny);
+      const int zz = b[2] + q;
+      zs[q] = WALLS ? ((zz < 0 || zz >= g.nz) ? -1 : zz) : wrap_int(zz, g.nz);
     }
+    const C cgg[3] = {C(a.cg * a.gvec[0]), C(a.cg * a.gvec[1]), C(a.cg * a.gvec[2])};
+    C* nc = static_cast<C*>(a.ncache);
+    bool reuse = false;
+    if (a.cache == 2) {
+      const int4 cb = a.ncache_b[k];
+      reuse = cb.x == b[0] && cb.y == b[1] && cb.z == b[2];
+    }
+    if (a.cache != 0 && !reuse) a.ncache_b[k] = make_int4(b[0], b[1], b[2], 0);
+    // node (kx, ky, kz) of slot k sits at nc[((kz SN + ky) SN + kx) M + k] (x 4)
+    if (SN == 2) {
+#pragma unroll
+      for (int kz = 0; kz < SN; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < SN; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < SN; ++kx) {
+            if (WALLS && zs[kz] < 0) continue;
+            const C wt = w[0][kx] * (w[1][ky] * w[2][kz]);
+            C* slot = nc + (((kz * SN + ky) * SN + kx) * M + k) * 4;
+            gather_node<S, WALLS>(a, g, xs[kx], ys[ky], zs[kz], wt, reuse, slot, cgg, own);
+          }
+    } else {
 #pragma unroll 1
-    for (int kz = 0; kz < SN; ++kz) {
-      int zz = b[2] + kz;
-      if (WALLS) {
-        if (zz < 0 || zz >= g.nz) continue;
-      } else {
-        zz = wrap_int(zz, g.nz);
-      }
+      for (int kz = 0; kz < SN; ++kz) {
+        if (WALLS && zs[kz] < 0) continue;
 #pragma unroll 1
-      for (int ky = 0; ky < SN; ++ky) {
-        const C wyz = w[1][ky] * w[2][kz];
+        for (int ky = 0; ky < SN; ++ky) {
+          const C wyz = w[1][ky] * w[2][kz];
 #pragma unroll 2
-        for (int kx = 0; kx < SN; ++kx) {
-          C u[3];
-          node_velocity<S, WALLS>(a, g, xs[kx], ys[ky], zz, u);
-          const C wt = w[0][kx] * wyz;
-          own[0] += wt * u[0]; own[1] += wt * u[1]; own[2] += wt * u[2];
+          for (int kx = 0; kx < SN; ++kx) {
+            C* slot = nc + (((kz * SN + ky) * SN + kx) * M + k) * 4;
+            gather_node<S, WALLS>(a, g, xs[kx], ys[ky], zs[kz], w[0][kx] * wyz, reuse, slot, cgg, own);
+          }
         }
       }
     }
   }
 
-  // ---- own marker: coupling / advection update (FP64 integration)
+  // ---- own marker: coupling / advection update (FP64 integration),
+  // stencil record and tile claims
   const double s = a.s;
   C Frec[3] = {C(0), C(0), C(0)};
   switch (a.mode) {
     case GM_COUPLE: {
-      const double im = a.inv_mass[i];
-      C dv[3], Fi[3];
-      double v[3];
-      for (int c = 0; c < 3; ++c) {
-        v[c] = a.vel[c * M + i];
-        dv[c] = (C)(v[c] - (double)own[c]);
-        Fi[c] = a.include_int ? (C)a.fint[c * M + i] : C(0);
-      }
+      C dv[3];
+      for (int c = 0; c < 3; ++c) dv[c] = (C)(v[c] - (double)own[c]);
       C Fh[3];
       const C cs = C(s), cim = C(im), crho = C(a.rho0);
       if (a.kind == 4) {                      // modified EBF, Eq. [modified-ebf]
@@ -478,104 +575,112 @@ __global__ void __launch_bounds__(128, 4) gather_kernel(const PartArgs p, const 
       for (int c = 0; c < 3; ++c)
         a.pos[c * M + i] = wrap_axis(a.pos[c * M + i] + s * (double)own[c], n3[c], per[c]);
       if (a.mode == GM_IBM_HALF)
-        for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * (C)a.fint[c * M + i];
+        for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * Fi[c];
       break;
     case GM_IBM1:
-      for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * (C)a.fint[c * M + i];
+      for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * Fi[c];
       break;
     default:
       break;
   }
   if (a.rec && (a.mode == GM_COUPLE || a.mode == GM_IBM_HALF || a.mode == GM_IBM1)) {
-    StencilRecT<C> r;
-    r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
-    for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
-    r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
-    r.pad = C(0);
-    static_cast<StencilRecT<C>*>(a.rec)[k] = r;
-    a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
-    // claim the tiles the stencil reaches (nodes with non-zero weight); per
-    // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
-    // node's tile or carries no weight
-    int tq[3][4];
+    unsigned long long claimed = 0ull;   // bit (qz SN + qy) SN + qx
+    int nclaim = 0;
+    int tq[3][SN];
+    {
+      StencilRecT<C> r;
+      r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
+      for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
+      r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
+      r.pad = C(0);
+      static_cast<StencilRecT<C>*>(a.rec)[k] = r;
+      a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+      // claim the tiles the stencil reaches (nodes with non-zero weight); per
+      // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
+      // node's tile or carries no weight
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < 3; ++c) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int t = -1;
-        if (q < SN && w[c][q] != C(0)) {
-          int node = b[c] + q;
-          if (per[c]) node = wrap_int(node, n3[c]);
-          if (node >= 0 && node < n3[c]) t = node >> TILE_SHIFT;
+        for (int q = 0; q < SN; ++q) {
+          int t = -1;
+          if (w[c][q] != C(0)) {
+            int node = b[c] + q;
+            if (per[c]) node = wrap_int(node, n3[c]);
+            if (node >= 0 && node < n3[c]) t = node >> TILE_SHIFT;
+          }
+#pragma unroll
+          for (int e = 0; e < q; ++e) if (tq[c][e] == t) t = -1;
+          tq[c][q] = t;
         }
+      }
 #pragma unroll
-        for (int e = 0; e < q; ++e) if (tq[c][e] == t) t = -1;
-        tq[c][q] = t;
+      for (int qz = 0; qz < SN; ++qz)
+#pragma unroll
+        for (int qy = 0; qy < SN; ++qy)
+#pragma unroll
+          for (int qx = 0; qx < SN; ++qx)
+            if (tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
+              uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
+              if (atomicExch(m, 1u) == 0u) {
+                claimed |= 1ull << ((qz * SN + qy) * SN + qx);
+                ++nclaim;
+              }
+            }
+      if (a.keys) {
+        // the bins of this step are valid while the marker stays within one
+        // cell of its home tile
+        const int t = home;
+        const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+          int cell = (int)floor(X[c]);
+          if (!per[c]) cell = cell < 0 ? 0 : (cell >= n3[c] ? n3[c] - 1 : cell);
+          const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
+          ok = ok && near_home(cell, lo, hi, n3[c], per[c]);
+        }
+        if (!ok) *a.status = 1;
       }
     }
-    unsigned long long claimed = 0ull;   // bit qz * 16 + qy * 4 + qx
-    int nclaim = 0;
-#pragma unroll
-    for (int qz = 0; qz < 4; ++qz)
-#pragma unroll
-      for (int qy = 0; qy < 4; ++qy)
-#pragma unroll
-        for (int qx = 0; qx < 4; ++qx)
-          if (tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
-            uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
-            if (*m == 0u && atomicExch(m, 1u) == 0u) {
-              claimed |= 1ull << (qz * 16 + qy * 4 + qx);
-              ++nclaim;
-            }
-          }
     // list slots for the claimed tiles, one atomic per warp; the lanes still
-    // running here are the warp's first nact lanes (slots k < M)
-    const int lane = threadIdx.x & 31;
+    // running are the warp's first nact lanes (slots k < M)
     const long long kw = k - lane;
     const int nact = M - kw >= 32 ? 32 : (int)(M - kw);
     const unsigned am = nact == 32 ? 0xffffffffu : ((1u << nact) - 1u);
     int incl = nclaim;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int v = __shfl_up_sync(am, incl, off);
-      if (lane >= off) incl += v;
+      const int u = __shfl_up_sync(am, incl, off);
+      if (lane >= off) incl += u;
     }
     const int total = __shfl_sync(am, incl, nact - 1);
     int base = 0;
     if (lane == nact - 1 && total > 0) base = atomicAdd(a.nlive, total);
     base = __shfl_sync(am, base, nact - 1) + incl - nclaim;
 #pragma unroll
-    for (int qz = 0; qz < 4; ++qz)
+    for (int qz = 0; qz < SN; ++qz)
 #pragma unroll
-      for (int qy = 0; qy < 4; ++qy)
+      for (int qy = 0; qy < SN; ++qy)
 #pragma unroll
-        for (int qx = 0; qx < 4; ++qx)
-          if (claimed & (1ull << (qz * 16 + qy * 4 + qx)))
-            a.live_tiles[base++] = (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
-    if (a.keys) {
-      // the bins of this step are valid while the marker stays within one
-      // cell of its home tile
-      const int t = (int)a.keys[k];
-      const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
-      bool ok = true;
-      for (int c = 0; c < 3; ++c) {
-        int cell = (int)floor(X[c]);
-        if (!per[c]) cell = cell < 0 ? 0 : (cell >= n3[c] ? n3[c] - 1 : cell);
-        const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
-        ok = ok && near_home(cell, lo, hi, n3[c], per[c]);
-      }
-      if (!ok) *a.status = 1;
-    }
+        for (int qx = 0; qx < SN; ++qx)
+          if (claimed & (1ull << ((qz * SN + qy) * SN + qx)))
+            a.live_tiles[base++] = make_int4((tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx],
+                                             tq[0][qx], tq[1][qy], tq[2][qz]);
   }
+}
+
+template <typename S, bool WALLS, bool REUSE>
+static void gather_str(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
+  const int bs = GATHER_THREADS;                // one marker per thread
+  const unsigned nb = (unsigned)((p.M + bs - 1) / bs);
+  if (p.stencil == 0) gather_kernel<S, WALLS, 0, REUSE><<<nb, bs, 0, s>>>(p, a);
+  else if (p.stencil == 1) gather_kernel<S, WALLS, 1, REUSE><<<nb, bs, 0, s>>>(p, a);
+  else gather_kernel<S, WALLS, 2, REUSE><<<nb, bs, 0, s>>>(p, a);
 }
 
 template <typename S, bool WALLS>
 static void gather_st(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
-  const int bs = 128;                          // one marker per thread
-  const unsigned nb = (unsigned)((p.M + bs - 1) / bs);
-  if (p.stencil == 0) gather_kernel<S, WALLS, 0><<<nb, bs, 0, s>>>(p, a);
-  else if (p.stencil == 1) gather_kernel<S, WALLS, 1><<<nb, bs, 0, s>>>(p, a);
-  else gather_kernel<S, WALLS, 2><<<nb, bs, 0, s>>>(p, a);
+  if (a.cache == 2) gather_str<S, WALLS, true>(p, a, s);
+  else gather_str<S, WALLS, false>(p, a, s);
 }
 
 template <typename S>
@@ -654,6 +759,33 @@ __device__ inline void tile_weights(int b, const C (&w)[4], int n, bool periodic
   }
 }
 
+// Offset of a stencil base from the tile origin, b - lo, taken as the
+// image in [-n/2, n/2) on a periodic axis.  On an axis of n >= 2 TILE cells
+// (or a wall-bounded one) node b + k then sits at local cell e + k of the
+// tile if 0 <= e + k < TILE, and no two nodes share a cell.
+__device__ inline int tile_offset(int b, int lo, int n, bool periodic) {
+  int e = b - lo;
+  if (periodic) {
+    const int h = n >> 1;
+    if (e < -h) e += n;
+    else if (e >= n - h) e -= n;
+  }
+  return e;
+}
+
+// the same weights as tile_weights for such an axis: out[j] = w[j - e]
+template <int SN, typename C>
+__device__ inline void tile_weights_shift(int e, const C (&w)[4], C (&out)[TILE]) {
+#pragma unroll
+  for (int j = 0; j < TILE; ++j) {
+    const int q = j - e;
+    C v = C(0);
+#pragma unroll
+    for (int k = 0; k < SN; ++k) v = q == k ? w[k] : v;
+    out[j] = v;
+  }
+}
+
 // a surviving marker reduced to the current tile: per axis the weights at
 // the tile's TILE cells, and its force
 template <typename C>
@@ -698,9 +830,12 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   __syncthreads();
   const int nlive = s_nlive;
   const int cxl = lane & 3, cyl = (lane >> 2) & 3, czl = lane >> 4;
+  // axes on which a stencil meets a tile only by shifting (see tile_offset)
+  const bool shx = g.nx >= 2 * TILE, shy = g.ny >= 2 * TILE, shz = !perz || g.nz >= 2 * TILE;
   for (int j = blockIdx.x * WARPS + wid; j < nlive; j += gridDim.x * WARPS) {
-    const int t = a.live_tiles[j];
-    const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+    const int4 lt = a.live_tiles[j];
+    const int t = lt.x;
+    const int tt[3] = {lt.y, lt.z, lt.w};
     const int lo[3] = {tt[0] * TILE, tt[1] * TILE, tt[2] * TILE};
     const int hi[3] = {min(lo[0] + TILE, g.nx) - 1, min(lo[1] + TILE, g.ny) - 1, min(lo[2] + TILE, g.nz) - 1};
     const int x = lo[0] + cxl, y = lo[1] + cyl, z0 = lo[2] + czl, z1 = z0 + 2;
@@ -710,6 +845,7 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
     const long long cell1 = cell0 + 2 * g.plane;
     C acc0[3] = {C(0), C(0), C(0)}, acc1[3] = {C(0), C(0), C(0)};
     if (a.accumulate && a.flag[t]) {
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (in0) acc0[c] = F[c * g.qstride + cell0];
         if (in1) acc1[c] = F[c * g.qstride + cell1];
@@ -717,6 +853,7 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
     }
     // neighbour tiles per axis: lane q < 8 reads entry q of each table row
     int rowv[3], nt[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int* row = a.ntab + (d * a.maxnt + tt[d]) * MAXNT;
       rowv[d] = lane < MAXNT ? row[lane] : -1;
@@ -755,23 +892,36 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
         const int kq = __shfl_sync(0xffffffffu, kb, pos);
         const int kk = kq + (cidx - ex);
         bool hit = false;
+        int e[3] = {0, 0, 0};
         if (cidx < total) {
           const short4 r = a.reach[kk];
-          hit = axis_reach<SN>(r.x, g.nx, true, lo[0], hi[0]) &&
-                axis_reach<SN>(r.y, g.ny, true, lo[1], hi[1]) &&
-                axis_reach<SN>(r.z, g.nz, perz, lo[2], hi[2]);
+          e[0] = tile_offset(r.x, lo[0], g.nx, true);
+          e[1] = tile_offset(r.y, lo[1], g.ny, true);
+          e[2] = tile_offset(r.z, lo[2], g.nz, perz);
+          hit = (shx ? e[0] <= hi[0] - lo[0] && e[0] + SN - 1 >= 0
+                     : axis_reach<SN>(r.x, g.nx, true, lo[0], hi[0])) &&
+                (shy ? e[1] <= hi[1] - lo[1] && e[1] + SN - 1 >= 0
+                     : axis_reach<SN>(r.y, g.ny, true, lo[1], hi[1])) &&
+                (shz ? e[2] <= hi[2] - lo[2] && e[2] + SN - 1 >= 0
+                     : axis_reach<SN>(r.z, g.nz, perz, lo[2], hi[2]));
         }
         unsigned mask = __ballot_sync(0xffffffffu, hit);
         if (hit) {
           const StencilRecT<C>& r = recs[kk];
           SpreadHit<C>& h = stage[lane];
           C rw[4];
-          for (int e = 0; e < 4; ++e) rw[e] = r.wx[e];
-          tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
-          for (int e = 0; e < 4; ++e) rw[e] = r.wy[e];
-          tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
-          for (int e = 0; e < 4; ++e) rw[e] = r.wz[e];
-          tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rw[q] = r.wx[q];
+          if (shx) tile_weights_shift<SN, C>(e[0], rw, h.w[0]);
+          else tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rw[q] = r.wy[q];
+          if (shy) tile_weights_shift<SN, C>(e[1], rw, h.w[1]);
+          else tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rw[q] = r.wz[q];
+          if (shz) tile_weights_shift<SN, C>(e[2], rw, h.w[2]);
+          else tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
           h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
         }
         __syncwarp();
@@ -788,6 +938,7 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
         __syncwarp();
       }
     }
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (in0) F[c * g.qstride + cell0] = acc0[c];
       if (in1) F[c * g.qstride + cell1] = acc1[c];
