@@ -148,7 +148,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch.distributed as dist
 
     torch.cuda.set_device(local_rank)
-    c, pos, bonds = workload()
+    c, pos, bonds = workload(scale=args.scale)
     nx, ny, nz = c["box"]
     cells = nx * ny * nz
     M, B = len(pos), len(bonds)
@@ -244,7 +244,8 @@ def run_gpu(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded bead chains, fluid at rest)",
-        "config": {"workload": WORKLOAD, "box": [nx, ny, nz], "collision": "mrt",
+        "config": {"workload": WORKLOAD if args.scale == 1 else "%s/%d" % (WORKLOAD, args.scale),
+                   "box": [nx, ny, nz], "collision": "mrt",
                    "tau": c["tau"], "storage": "f32 deviations", "particles": M,
                    "bonds": B, "coupling": "force coupling, gamma=5, m=1",
                    "stencil": "trilinear", "split": "Eq. multistep, n=4 coupled sub-steps per half",
@@ -346,6 +347,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    # box edge / SCALE and particle count / SCALE^3 at the same densities: the
+    # small case for multi-pass profiler captures (default: the full workload)
+    ap.add_argument("--scale", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -45,7 +45,7 @@ template <> struct Store<__nv_bfloat16> {
 // pre-streaming array (periodic in x, y; z periodic or bounce-back).
 template <typename S, bool WALLS>
 __device__ inline void pull_cell(const S* __restrict__ f, const Geom& g,
-                                 const double* bb_bot, const double* bb_top,
+                                 const Real* bb_bot, const Real* bb_top,
                                  float sc, int x, int y, int z,
                                  typename Store<S>::C (&out)[Q]) {
   using C = typename Store<S>::C;
@@ -67,8 +67,8 @@ __device__ inline void pull_cell(const S* __restrict__ f, const Geom& g,
     if (WALLS && cz != 0 && (zs < 0 || zs >= g.nz)) {
       // bounced back at the wall: population opp(i) of this cell, plus the
       // moving-wall momentum term
-      const double bb = cz > 0 ? bb_bot[i] : bb_top[i];
-      out[i] = Store<S>::load(f, opp_of(i) * g.qstride + cell, opp_of(i), sc) + C(bb);
+      const C bb = rv<C>(cz > 0 ? bb_bot[i] : bb_top[i]);
+      out[i] = Store<S>::load(f, opp_of(i) * g.qstride + cell, opp_of(i), sc) + bb;
     } else {
       out[i] = Store<S>::load(f, i * g.qstride + zs * g.plane + (long long)ys * g.pitch + xs, i, sc);
     }

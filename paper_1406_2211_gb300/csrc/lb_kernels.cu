@@ -143,7 +143,7 @@ __device__ inline void back_all(const C (&m)[Q], C (&post)[Q]) {
 }
 
 template <typename S, int COLL, bool WALLS, bool FORCED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
 lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
   using C = typename Store<S>::C;
   const Geom& g = a.g;
@@ -163,23 +163,25 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     if (cy_of(i)) jy += C(cy_of(i)) * f[i];
     if (cz_of(i)) jz += C(cz_of(i)) * f[i];
   }
-  const C rho = C(a.rho0) + rd;
+  const C rho = rv<C>(a.rho0) + rd;
   const C inv = C(1) / rho;
   const C u0x = jx * inv, u0y = jy * inv, u0z = jz * inv;
-  C Fx = C(a.cg * a.gvec[0]), Fy = C(a.cg * a.gvec[1]), Fz = C(a.cg * a.gvec[2]);
+  C Fx = rv<C>(a.cgg[0]), Fy = rv<C>(a.cgg[1]), Fz = rv<C>(a.cgg[2]);
   if (FORCED) {
     const int t = tile_of(g, x, y, z);
     const C* Fa = static_cast<const C*>(a.Fa);
     const C* Fb = static_cast<const C*>(a.Fb);
     if (Fa && a.flag_a[t]) {
-      Fx += C(a.ca) * Fa[cell];
-      Fy += C(a.ca) * Fa[g.qstride + cell];
-      Fz += C(a.ca) * Fa[2 * g.qstride + cell];
+      const C ca = rv<C>(a.ca);
+      Fx += ca * Fa[cell];
+      Fy += ca * Fa[g.qstride + cell];
+      Fz += ca * Fa[2 * g.qstride + cell];
     }
     if (Fb && a.flag_b[t]) {
-      Fx += C(a.cb) * Fb[cell];
-      Fy += C(a.cb) * Fb[g.qstride + cell];
-      Fz += C(a.cb) * Fb[2 * g.qstride + cell];
+      const C cb = rv<C>(a.cb);
+      Fx += cb * Fb[cell];
+      Fy += cb * Fb[g.qstride + cell];
+      Fz += cb * Fb[2 * g.qstride + cell];
     }
   }
   const C u1x = u0x + Fx * inv, u1y = u0y + Fy * inv, u1z = u0z + Fz * inv;
@@ -190,7 +192,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   if (COLL == 0) {
     // f*_i = gamma fbar_i + n_i [ (1-gamma) rd/36 + c_i.((1-gamma) j + F)/12
     //                             + rho (Q_i(u1) - gamma Q_i(u0)) ]
-    const C gam = C(a.gamma_bgk);
+    const C gam = rv<C>(a.gamma_bgk);
     const C omg = C(1) - gam;
     const C sm = div_by<C, 36>(omg * rd);
     const C qx = div_by<C, 12>(omg * jx + Fx), qy = div_by<C, 12>(omg * jy + Fy),
@@ -217,7 +219,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     const C nzz = pzz - r3 - rho * u0z * u0z;
     const C nxy = pxy - rho * u0x * u0y, nyz = pyz - rho * u0y * u0z, nxz = pxz - rho * u0x * u0z;
     const C tr = nxx + nyy + nzz;
-    const C gb = C(a.gamma_k[0]), gs = C(a.gamma_k[1]);
+    const C gb = rv<C>(a.gamma_k[0]), gs = rv<C>(a.gamma_k[1]);
     C m[Q];
     m[4] = tr * (gb * C(1.0 / mrt_b(4)));
     m[5] = (C(3) * nxx - tr) * (gs * C(1.0 / mrt_b(5)));
@@ -254,7 +256,8 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
                                     rho * quad_part<C, i>(u0x, u0y, u0z, uu0));
     };
     unroll_q(fill);
-    const C gk[5] = {C(0), C(a.gamma_k[0]), C(a.gamma_k[1]), C(a.gamma_k[2]), C(a.gamma_k[3])};
+    const C gk[5] = {C(0), rv<C>(a.gamma_k[0]), rv<C>(a.gamma_k[1]), rv<C>(a.gamma_k[2]),
+                      rv<C>(a.gamma_k[3])};
     C m[Q];
     moments_all<C>(neq, gk, m);
     C post[Q];
@@ -287,7 +290,7 @@ static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream
   if (a.collision == 0) {
     if (a.g.walls) { if (forced) LBC_LAUNCH(0, true, true); else LBC_LAUNCH(0, true, false); }
     else { if (forced) LBC_LAUNCH(0, false, true); else LBC_LAUNCH(0, false, false); }
-  } else if (a.gamma_k[2] == 0.0 && a.gamma_k[3] == 0.0) {
+  } else if (a.gamma_k[2].d == 0.0 && a.gamma_k[3].d == 0.0) {
     if (a.g.walls) { if (forced) LBC_LAUNCH(2, true, true); else LBC_LAUNCH(2, true, false); }
     else { if (forced) LBC_LAUNCH(2, false, true); else LBC_LAUNCH(2, false, false); }
   } else {
@@ -323,8 +326,8 @@ __global__ void unstream_kernel(const S* __restrict__ fbar, S* __restrict__ fsta
     C v;
     if (g.walls && (zt < 0 || zt >= g.nz)) {
       const int o = opp_of(j);
-      const double bb = zt < 0 ? a.bb_bot[o] : a.bb_top[o];
-      v = Store<S>::load(fbar, o * g.qstride + cell, o, a.scale16) - C(bb);
+      const C bb = rv<C>(zt < 0 ? a.bb_bot[o] : a.bb_top[o]);
+      v = Store<S>::load(fbar, o * g.qstride + cell, o, a.scale16) - bb;
     } else {
       const int xt = wrap_int(x + cx_of(j), g.nx);
       const int yt = wrap_int(y + cy_of(j), g.ny);
@@ -373,7 +376,7 @@ __global__ void fields_kernel(const S* __restrict__ fstar, const LBArgs a, doubl
     j[1] += cy_of(i) * double(f[i]);
     j[2] += cz_of(i) * double(f[i]);
   }
-  const double rho = a.rho0 + rd;
+  const double rho = a.rho0.d + rd;
   const int t = tile_of(g, x, y, z);
   const C* Fa = static_cast<const C*>(a.Fa);
   const bool fa = Fa != nullptr && a.flag_a[t];
@@ -526,7 +529,7 @@ __global__ void init_eq_kernel(const double* __restrict__ rho, const double* __r
   for (int i = 0; i < Q; ++i) {
     const double cu = cx_of(i) * v0 + cy_of(i) * v1 + cz_of(i) * v2;
     const double w = w_of(i);
-    const double dev = w * (r - a.rho0) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    const double dev = w * (r - a.rho0.d) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
     Store<S>::store(dst, i * g.qstride + cell, typename Store<S>::C(dev), i, a.scale16);
   }
 }

@@ -199,16 +199,16 @@ void fill_lb_args(lbc_box* b) {
   const lbc_lattice_desc& l = b->lat;
   a.g = b->L.g;
   a.collision = l.collision;
-  a.rho0 = l.rho0;
-  a.gamma_bgk = 1.0 - 1.0 / l.tau;
+  a.rho0 = make_real(l.rho0);
+  a.gamma_bgk = make_real(1.0 - 1.0 / l.tau);
   const double lam_s = l.mrt_lambda[0] != 0.0 ? l.mrt_lambda[0] : 1.0 / l.tau;
   const double lam_b = l.mrt_lambda[1] != 0.0 ? l.mrt_lambda[1] : lam_s;
   const double lam_go = l.mrt_lambda[2] != 0.0 ? l.mrt_lambda[2] : 1.0;
   const double lam_ge = l.mrt_lambda[3] != 0.0 ? l.mrt_lambda[3] : 1.0;
-  a.gamma_k[0] = 1.0 - lam_b;
-  a.gamma_k[1] = 1.0 - lam_s;
-  a.gamma_k[2] = 1.0 - lam_go;
-  a.gamma_k[3] = 1.0 - lam_ge;
+  a.gamma_k[0] = make_real(1.0 - lam_b);
+  a.gamma_k[1] = make_real(1.0 - lam_s);
+  a.gamma_k[2] = make_real(1.0 - lam_go);
+  a.gamma_k[3] = make_real(1.0 - lam_ge);
   for (int c = 0; c < 3; ++c) a.gvec[c] = l.body_force[c];
   for (int i = 0; i < Q; ++i) {
     const double w = w_of(i);
@@ -216,8 +216,8 @@ void fill_lb_args(lbc_box* b) {
                         cz_of(i) * l.wall_velocity[0][2];
     const double cu_t = cx_of(i) * l.wall_velocity[1][0] + cy_of(i) * l.wall_velocity[1][1] +
                         cz_of(i) * l.wall_velocity[1][2];
-    a.bb_bot[i] = l.z_walls ? 6.0 * w * l.rho0 * cu_b : 0.0;
-    a.bb_top[i] = l.z_walls ? 6.0 * w * l.rho0 * cu_t : 0.0;
+    a.bb_bot[i] = make_real(l.z_walls ? 6.0 * w * l.rho0 * cu_b : 0.0);
+    a.bb_top[i] = make_real(l.z_walls ? 6.0 * w * l.rho0 * cu_t : 0.0);
   }
   a.scale16 = (float)(l.storage_scale != 0.0 ? l.storage_scale : 1.0);
 }
@@ -245,7 +245,8 @@ struct Plan {
     LBArgs a = b->lb;
     a.Fa = Fa; a.flag_a = Fa ? (Fa == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.Fb = Fb; a.flag_b = Fb ? (Fb == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
-    a.ca = ca; a.cb = cb; a.cg = cg;
+    a.ca = make_real(ca); a.cb = make_real(cb);
+    for (int c = 0; c < 3; ++c) a.cgg[c] = make_real(cg * b->lat.body_force[c]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->timing_cap > 0) {
       if (b->capturing) {
@@ -314,14 +315,14 @@ struct Plan {
     GatherArgs a{};
     a.kind = b->cpl.kind;
     a.order = b->cpl.order;
-    a.gamma = b->cpl.gamma;
-    a.rho0 = b->lat.rho0;
-    a.rho0_pop = b->lat.rho0;
+    a.gamma = make_real(b->cpl.gamma);
+    a.rho0 = make_real(b->lat.rho0);
+    a.rho0_pop = make_real(b->lat.rho0);
     a.pops = b->pop(b->cur);
     a.storage = b->lat.storage;
     a.scale16 = b->lb.scale16;
     for (int i = 0; i < Q; ++i) { a.bb_bot[i] = b->lb.bb_bot[i]; a.bb_top[i] = b->lb.bb_top[i]; }
-    for (int c = 0; c < 3; ++c) a.gvec[c] = b->lat.body_force[c];
+    for (int c = 0; c < 3; ++c) a.cgg[c] = make_real(0.0);
     a.perm = b->uptr(b->L.off_idx[0]);
     a.pos = b->dptr(b->L.off_pos[b->pc]);
     a.vel = b->dptr(b->L.off_vel[b->pc]);
@@ -342,9 +343,9 @@ struct Plan {
   }
 
   void fields(GatherArgs& a, int f1, double c1, int f2, double c2, double cg) {
-    a.F1 = f1 >= 0 ? b->F(f1) : nullptr; a.flag1 = f1 >= 0 ? b->flag(f1) : nullptr; a.c1 = c1;
-    a.F2 = f2 >= 0 ? b->F(f2) : nullptr; a.flag2 = f2 >= 0 ? b->flag(f2) : nullptr; a.c2 = c2;
-    a.cg = cg;
+    a.F1 = f1 >= 0 ? b->F(f1) : nullptr; a.flag1 = f1 >= 0 ? b->flag(f1) : nullptr; a.c1 = make_real(c1);
+    a.F2 = f2 >= 0 ? b->F(f2) : nullptr; a.flag2 = f2 >= 0 ? b->flag(f2) : nullptr; a.c2 = make_real(c2);
+    for (int c = 0; c < 3; ++c) a.cgg[c] = make_real(cg * b->lat.body_force[c]);
   }
 
   void gather(const GatherArgs& a) {
@@ -395,19 +396,19 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     if (order2(b)) {
       // Sec. 5.1: predictor Xt, F = F_int(Xt), two half advections around LB
       GatherArgs a = P.gather_base();
-      a.mode = GM_IBM_PREDICT; a.s = 0.5 * h; a.perm = nullptr;
+      a.mode = GM_IBM_PREDICT; a.s = make_real(0.5 * h); a.perm = nullptr;
       P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
       P.gather(a);
       P.drift(0.0, 0.0, 0.0, true, true, false, b->dptr(b->L.off_aux));
       P.sort();
       a = P.gather_base();
-      a.mode = GM_IBM_HALF; a.s = 0.5 * h; a.rec_weight = 1.0;
+      a.mode = GM_IBM_HALF; a.s = make_real(0.5 * h); a.rec_weight = make_real(1.0);
       P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
       P.gather(a);
       P.spread(ib, false);
       P.lb(b->F(ia), b->F(ib), 0.5 * h, 0.5 * h, h);
       a = P.gather_base();
-      a.mode = GM_IBM_FINAL; a.s = 0.5 * h;
+      a.mode = GM_IBM_FINAL; a.s = make_real(0.5 * h);
       P.fields(a, ib, 0.5 * h, -1, 0.0, 0.5 * h);
       P.gather(a);
       b->ia = ib;
@@ -415,12 +416,12 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
       P.drift(0.0, 0.0, 0.0, true, true, false);
       P.sort();
       GatherArgs a = P.gather_base();
-      a.mode = GM_IBM1; a.rec_weight = 1.0;
+      a.mode = GM_IBM1; a.rec_weight = make_real(1.0);
       P.gather(a);
       P.spread(ib, false);
       P.lb(nullptr, b->F(ib), 0.0, h, h);
       a = P.gather_base();
-      a.mode = GM_ADVECT; a.s = h; a.perm = nullptr;
+      a.mode = GM_ADVECT; a.s = make_real(h); a.perm = nullptr;
       P.fields(a, -1, 0.0, -1, 0.0, 0.0);
       P.gather(a);
     }
@@ -434,7 +435,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     P.drift(0.0, 0.0, 0.0, true, true);
     P.sort();
     GatherArgs a = P.gather_base();
-    a.mode = GM_COUPLE; a.s = h; a.include_int = 1; a.rec_weight = 1.0;
+    a.mode = GM_COUPLE; a.s = make_real(h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
     P.gather(a);
     P.spread(ib, false);
@@ -449,13 +450,13 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     P.drift(0.5 * h, 0.0, 0.0, true, true);
     P.sort();
     GatherArgs a = P.gather_base();
-    a.mode = GM_COUPLE; a.s = 0.5 * h; a.include_int = 1; a.rec_weight = 1.0;
+    a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
     P.gather(a);
     P.spread(ib, false);
     P.lb(b->F(ia), b->F(ib), 0.5 * h, 0.5 * h, h);
     a = P.gather_base();
-    a.mode = GM_COUPLE; a.s = 0.5 * h; a.include_int = 1; a.rec_weight = 1.0;
+    a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
     P.gather(a);
     P.spread(ia, false);
@@ -477,7 +478,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
           P.drift(0.5 * dt, 0.0, 0.0, true, false, true, nullptr, 0.5 * dt);
         }
         GatherArgs a = P.gather_base();
-        a.mode = GM_COUPLE; a.s = dt; a.include_int = 1; a.rec_weight = 1.0 / n;
+        a.mode = GM_COUPLE; a.s = make_real(dt); a.include_int = 1; a.rec_weight = make_real(1.0 / n);
         // the populations and the fixed field are the same for the n
         // sub-steps of a half: node moments are stored at the first one
         if (b->L.use_ncache) a.cache = k == 0 ? 1 : 2;
@@ -502,7 +503,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
       P.sort();
     }
     GatherArgs a = P.gather_base();
-    a.mode = GM_COUPLE; a.s = 0.5 * h; a.include_int = 0; a.rec_weight = 1.0;
+    a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 0; a.rec_weight = make_real(1.0);
     P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
     P.gather(a);
     P.spread(ib, false);
@@ -511,7 +512,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     for (int k = 0; k < n; ++k) P.drift(0.5 * dt, dt, 0.5 * dt, true, k == n - 1);
     P.sort();
     a = P.gather_base();
-    a.mode = GM_COUPLE; a.s = 0.5 * h; a.include_int = 0; a.rec_weight = 1.0;
+    a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 0; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
     P.gather(a);
     P.spread(ia, false);

@@ -75,6 +75,19 @@ __host__ __device__ constexpr int mrt_group(int k) {
   return k < 4 ? 0 : (k == 4 ? 1 : (k < 10 ? 2 : (k < 16 ? 3 : 4)));
 }
 
+// A scalar kernel argument in both compute types.  Kernels take the one of
+// their compute type, so no thread converts a double to a float (on this
+// GPU the conversion runs on the FP64 pipe, at a small fraction of the FP32
+// rate).
+struct Real {
+  double d;
+  float f;
+};
+inline Real make_real(double v) { return Real{v, static_cast<float>(v)}; }
+template <typename C> __host__ __device__ inline C rv(const Real& r);
+template <> __host__ __device__ inline float rv<float>(const Real& r) { return r.f; }
+template <> __host__ __device__ inline double rv<double>(const Real& r) { return r.d; }
+
 // Box geometry.  Populations are SoA: pop i of cell (x, y, z) lives at
 // i * qstride + z * plane + y * pitch + x, with pitch >= nx padded so rows
 // start on 32-byte boundaries.

@@ -11,18 +11,18 @@ namespace lbc {
 
 enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
-// Arguments of the fused LB step (all scalars in double; each kernel
-// converts to its compute type).
+// Arguments of the fused LB step (scalars in both compute types).
 struct LBArgs {
   Geom g;
   int collision;          // 0 BGK, 1 MRT
-  double rho0;
-  double gamma_bgk;       // 1 - 1/tau
-  double gamma_k[4];      // MRT 1 - lambda: bulk, shear, odd ghost, even ghost
-  double ca, cb, cg;      // u1 = u0 + (ca F_a + cb F_b + cg g) / rho
+  Real rho0;
+  Real gamma_bgk;         // 1 - 1/tau
+  Real gamma_k[4];        // MRT 1 - lambda: bulk, shear, odd ghost, even ghost
+  Real ca, cb;            // u1 = u0 + (ca F_a + cb F_b + cg g) / rho
+  Real cgg[3];            // cg g
   double gvec[3];         // uniform body force density g
-  double bb_bot[Q];       // moving-wall term of population i arriving from
-  double bb_top[Q];       //   the bottom / top wall: 6 w_i rho0 c_i . u_w
+  Real bb_bot[Q];         // moving-wall term of population i arriving from
+  Real bb_top[Q];         //   the bottom / top wall: 6 w_i rho0 c_i . u_w
   // sparse force fields (may be null): F[c * qstride + cell] in the compute
   // type of the storage (double for FP64 storage, float otherwise), one
   // activity flag per force tile
@@ -119,17 +119,18 @@ struct GatherArgs {
   int kind;             // 2 fc, 3 ebf, 4 mebf
   int order;            // 1 explicit drag, 2 Crank-Nicolson
   int include_int;      // F_int enters the coupling force and the kick
-  double s;             // step of this force / position update
-  double gamma, rho0;
-  double rec_weight;    // spread force = rec_weight * (-F^h) (or +F_int)
+  Real s;               // step of this force / position update
+  Real gamma, rho0;
+  Real rec_weight;      // spread force = rec_weight * (-F^h) (or +F_int)
   // fluid velocity (((j + c1 F1) + cg g) + c2 F2) / rho at the stencil
   // nodes; F1 stays fixed over the sub-steps of a half step, F2 is the field
   // being accumulated by them
   const void* pops; int storage; float scale16;
-  double bb_bot[Q]; double bb_top[Q];
-  const void* F1; const uint8_t* flag1; double c1;
-  const void* F2; const uint8_t* flag2; double c2;
-  double cg; double gvec[3]; double rho0_pop;
+  Real bb_bot[Q]; Real bb_top[Q];
+  const void* F1; const uint8_t* flag1; Real c1;
+  const void* F2; const uint8_t* flag2; Real c2;
+  Real cgg[3];          // cg g
+  Real rho0_pop;
   // per-slot cache of j + c1 F1 and 1 / rho at the stencil nodes, valid
   // while pops and F1 are unchanged: 0 unused, 1 store, 2 reuse where the
   // slot's stencil base is the stored one.  Layout [(node * 4 + c) * M + k];

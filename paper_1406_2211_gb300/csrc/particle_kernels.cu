@@ -366,11 +366,11 @@ __device__ inline void node_base(const GatherArgs& a, const Geom& g, int x, int 
   const C* F1 = static_cast<const C*>(a.F1);
   if (F1 && a.flag1[tile_of(g, x, y, z)]) {
     const long long cell = z * g.plane + (long long)y * g.pitch + x;
-    const C c1 = C(a.c1);
+    const C c1 = rv<C>(a.c1);
     j0 += c1 * F1[cell]; j1 += c1 * F1[g.qstride + cell]; j2 += c1 * F1[2 * g.qstride + cell];
   }
   j[0] = j0; j[1] = j1; j[2] = j2;
-  inv = C(1) / (C(a.rho0_pop) + rd);
+  inv = C(1) / (rv<C>(a.rho0_pop) + rd);
 }
 
 // is cell c within [lo - 1, hi + 1] of its home tile (periodic wrap)?
@@ -431,7 +431,7 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
   const C* F2 = static_cast<const C*>(a.F2);
   if (F2 && a.flag2[tile_of(g, x, y, z)]) {
     const long long cell = z * g.plane + (long long)y * g.pitch + x;
-    const C c2 = C(a.c2);
+    const C c2 = rv<C>(a.c2);
     j[0] += c2 * F2[cell]; j[1] += c2 * F2[g.qstride + cell]; j[2] += c2 * F2[2 * g.qstride + cell];
   }
   own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
@@ -494,7 +494,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       const int zz = b[2] + q;
       zs[q] = WALLS ? ((zz < 0 || zz >= g.nz) ? -1 : zz) : wrap_int(zz, g.nz);
     }
-    const C cgg[3] = {C(a.cg * a.gvec[0]), C(a.cg * a.gvec[1]), C(a.cg * a.gvec[2])};
+    const C cgg[3] = {rv<C>(a.cgg[0]), rv<C>(a.cgg[1]), rv<C>(a.cgg[2])};
     C* nc = static_cast<C*>(a.ncache);
     bool reuse = false;
     if (a.cache == 2) {
@@ -534,21 +534,21 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
 
   // ---- own marker: coupling / advection update (FP64 integration),
   // stencil record and tile claims
-  const double s = a.s;
+  const double s = a.s.d;
   C Frec[3] = {C(0), C(0), C(0)};
   switch (a.mode) {
     case GM_COUPLE: {
       C dv[3];
       for (int c = 0; c < 3; ++c) dv[c] = (C)(v[c] - (double)own[c]);
       C Fh[3];
-      const C cs = C(s), cim = C(im), crho = C(a.rho0);
+      const C cs = rv<C>(a.s), cim = C(im), crho = rv<C>(a.rho0);
       if (a.kind == 4) {                      // modified EBF, Eq. [modified-ebf]
         // r = 1/(1 + m/rho0) = rho0 im/(rho0 im + 1); 1/(s(1/m + 1/rho0))
         const C r = crho * cim / (crho * cim + C(1));
         const C inv = C(1) / (cs * (cim + C(1) / crho));
         for (int c = 0; c < 3; ++c) Fh[c] = -dv[c] * inv - r * Fi[c];
       } else {
-        const C gam = a.kind == 3 ? crho : C(a.gamma);   // EBF: rho a^3 / h
+        const C gam = a.kind == 3 ? crho : rv<C>(a.gamma);   // EBF: rho a^3 / h
         if (a.order == 1) {
           for (int c = 0; c < 3; ++c) Fh[c] = -gam * dv[c];
         } else {                              // Crank-Nicolson, Eq. [modified-force]
@@ -561,7 +561,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       for (int c = 0; c < 3; ++c) {
         a.vel[c * M + i] = v[c] + kick * (double)(Fh[c] + Fi[c]);
         if (a.fh_out) a.fh_out[c * M + i] = (double)Fh[c];
-        Frec[c] = -C(a.rec_weight) * Fh[c];
+        Frec[c] = -rv<C>(a.rec_weight) * Fh[c];
       }
       break;
     }
@@ -575,10 +575,10 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       for (int c = 0; c < 3; ++c)
         a.pos[c * M + i] = wrap_axis(a.pos[c * M + i] + s * (double)own[c], n3[c], per[c]);
       if (a.mode == GM_IBM_HALF)
-        for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * Fi[c];
+        for (int c = 0; c < 3; ++c) Frec[c] = rv<C>(a.rec_weight) * Fi[c];
       break;
     case GM_IBM1:
-      for (int c = 0; c < 3; ++c) Frec[c] = C(a.rec_weight) * Fi[c];
+      for (int c = 0; c < 3; ++c) Frec[c] = rv<C>(a.rec_weight) * Fi[c];
       break;
     default:
       break;
