@@ -77,14 +77,19 @@ def workload(scale=1):
     return c, pos, bonds
 
 
-def make_box(c, npart, nbonds):
+def make_box(c, npart, nbonds, storage=None):
     from paper_1406_2211_gb300 import lbc
     nx, ny, nz = c["box"]
     lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"],
-                           rho0=c["rho0"], body_force=c["body_force"], storage=c["storage"])
+                           rho0=c["rho0"], body_force=c["body_force"],
+                           storage=storage or c["storage"])
     cpl = lbc.coupling_desc(c["kind"], 2, c["stencil"], gamma=c["gamma"], split=c["mode"],
                             substeps=c["substeps"])
     return lbc.Box(lat, cpl, max_particles=npart, max_bonds=nbonds)
+
+
+# algorithmic bytes per cell update of the fused LB step: 19 reads + 19 writes
+BYTES_PER_CELL = {"f32": 2 * 19 * 4, "f16dev": 2 * 19 * 2, "bf16dev": 2 * 19 * 2, "f64": 2 * 19 * 8}
 
 
 # ------------------------------------------------------------------ clocks
@@ -154,64 +159,88 @@ def run_gpu(args, rank, world, local_rank):
     M, B = len(pos), len(bonds)
     stream = torch.cuda.current_stream()
 
-    box = make_box(c, M, B)
-    box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
-    box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
-                      bond_k=c["bond_k"], bond_r0=c["bond_r0"])
-    box.step(args.warmup)
-    from paper_1406_2211_gb300 import lbc
-    box.set_option(lbc.LBC_OPT_TIMING, args.steps + 4)
-    # the graphs are recaptured with timing nodes: one eager step + one
-    # replay before the timed region keeps capture out of it
-    box.step(3)
-    box.lb_timing(reset=True)
-    launches_per_step = box.launches_per_step()
+    def timed(storage, steps, sample_clocks):
+        """Warm up, then time `steps` coupled steps of a fresh box (CUDA
+        events on the launching stream, barrier + synchronize on both sides);
+        LB kernel launches are timed by event nodes inside the graphs."""
+        from paper_1406_2211_gb300 import lbc
+        box = make_box(c, M, B, storage)
+        box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+        box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
+                          bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+        box.step(args.warmup)
+        box.set_option(lbc.LBC_OPT_TIMING, steps + 4)
+        # the graphs are recaptured with timing nodes: one eager step + one
+        # replay before the timed region keeps capture out of it
+        box.step(3)
+        box.lb_timing(reset=True)
+        r = {"launches_per_step": box.launches_per_step(),
+             "pop_bytes": box.population_bytes()}
+        clocks = ClockSampler(local_rank) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        box.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        r["ms"] = e0.elapsed_time(e1)
+        r["clocks"] = clocks.stop() if clocks else None
+        r["lb_ms"], r["lb_n"] = box.lb_timing(reset=True)
+        _, _, st = box.invariants()
+        if st != 0:
+            raise RuntimeError("non-finite state after the timed steps (%s)" % storage)
+        if r["lb_n"] == 0 or r["lb_ms"] <= 0:
+            raise RuntimeError("no LB kernel launches were timed")
+        box.close()
+        del box
+        torch.cuda.empty_cache()
+        t = torch.tensor([r["ms"]], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r["ms_max"] = float(t.item())
+        r["value"] = world * cells * steps / (r["ms_max"] * 1e-3) / 1e6
+        r["lb_avg_ms"] = r["lb_ms"] / r["lb_n"]
+        r["achieved"] = BYTES_PER_CELL[storage] * cells / (r["lb_avg_ms"] * 1e-3) / 1e9
+        return r
 
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    box.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    lb_ms, lb_n = box.lb_timing(reset=True)
-    m_end, P_end, st = box.invariants()
-    if st != 0:
-        raise RuntimeError("non-finite state after the timed steps")
-
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    main = timed(c["storage"], args.steps, True)
+    ms, ms_max, value = main["ms"], main["ms_max"], main["value"]
+    lb_ms, lb_n, lb_avg_ms = main["lb_ms"], main["lb_n"], main["lb_avg_ms"]
+    launches_per_step, pop_bytes, clk = main["launches_per_step"], main["pop_bytes"], main["clocks"]
 
     # roofline of the dominant kernel (fused LB step): algorithmic bytes =
     # 2 x 19 populations x 4 bytes per cell
-    pop_bytes = box.population_bytes()
-    alg_bytes = 2 * 19 * 4 * cells
-    if lb_n == 0 or lb_ms <= 0:
-        raise RuntimeError("no LB kernel launches were timed")
-    lb_avg_ms = lb_ms / lb_n
-    achieved = alg_bytes / (lb_avg_ms * 1e-3) / 1e9
+    alg_bytes = BYTES_PER_CELL[c["storage"]] * cells
+    achieved = main["achieved"]
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic()
+
+    # the same coupled step with 16-bit population storage (deviations from
+    # w_i rho0, stochastic rounding, FP32 arithmetic)
+    forms = None
+    if not args.no_forms:
+        forms = {}
+        nform = min(args.steps, 100)
+        for st16 in ("f16dev", "bf16dev"):
+            r = timed(st16, nform, False)
+            forms[st16] = {"value": r["value"], "unit": "MLUPS", "steps": nform,
+                           "ms_per_step": r["ms_max"] / nform,
+                           "lb_avg_ms": r["lb_avg_ms"], "lb_achieved_gbs": r["achieved"],
+                           "lb_frac_of_peak": r["achieved"] / peak,
+                           "alg_bytes_per_cell": BYTES_PER_CELL[st16]}
 
     # end to end through the C ABI with host buffers: upload particles,
     # step, read particles and invariants back (copies inside the timing)
     e2e = None
     if not args.no_e2e:
-        box.close()
-        del box
-        torch.cuda.empty_cache()
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hpos, hvel = pin(pos), pin(np.zeros_like(pos))
         box2 = make_box(c, M, B)
@@ -262,6 +291,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clk,
         "e2e": e2e,
+        "storage_forms": forms,
     }
     return line
 
@@ -347,6 +377,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the 16-bit storage forms of the same step")
     # box edge / SCALE and particle count / SCALE^3 at the same densities: the
     # small case for multi-pass profiler captures (default: the full workload)
     ap.add_argument("--scale", type=int, default=1)

@@ -9,26 +9,43 @@
 namespace lbc {
 
 // ----------------------------------------------------------------- storage
+// load(p, k, i, sc): the deviation of population i stored at p[k].
+// store(p, k, v, i, rsc, r): store deviation v of population i at p[k]; rsc
+// is 1/scale and r 32 random bits, both used by the 16-bit forms only.
+// store_nearest: the same with round-to-nearest (layout conversions, where a
+// value already representable must come back unchanged).
 template <typename S> struct Store;
 template <> struct Store<double> {
   using C = double;
   __device__ static C load(const double* p, long long k, int, float) { return __ldg(p + k); }
-  __device__ static void store(double* p, long long k, C v, int, float) { p[k] = v; }
+  __device__ static void store(double* p, long long k, C v, int, float, uint32_t) { p[k] = v; }
+  __device__ static void store_nearest(double* p, long long k, C v, int, float) { p[k] = v; }
 };
 template <> struct Store<float> {
   using C = float;
   __device__ static C load(const float* p, long long k, int, float) { return __ldg(p + k); }
-  __device__ static void store(float* p, long long k, C v, int, float) { p[k] = v; }
+  __device__ static void store(float* p, long long k, C v, int, float, uint32_t) { p[k] = v; }
+  __device__ static void store_nearest(float* p, long long k, C v, int, float) { p[k] = v; }
 };
 // 16-bit forms store dev / (w_i * scale) so every population uses the same
-// dynamic range
+// dynamic range, rounded stochastically: random bits are added below the last
+// kept bit of the FP32 pattern and the sum is truncated, so a value is
+// rounded up in magnitude with probability equal to its distance from the
+// truncated value in units of the 16-bit spacing.  The rounding error then
+// has zero mean and does not build up systematically from step to step.
+// (FP16 values below the FP16 normal range are truncated with the same 13
+// random bits, which is unbiased only to within their own spacing.)
 template <> struct Store<__half> {
   using C = float;
   __device__ static C load(const __half* p, long long k, int i, float sc) {
     return __half2float(p[k]) * (float(w_of(i)) * sc);
   }
-  __device__ static void store(__half* p, long long k, C v, int i, float sc) {
-    p[k] = __float2half_rn(v / (float(w_of(i)) * sc));
+  __device__ static void store(__half* p, long long k, C v, int i, float rsc, uint32_t r) {
+    const float x = v * (float(1.0 / w_of(i)) * rsc);
+    p[k] = __float2half_rz(__uint_as_float(__float_as_uint(x) + (r & 0x1FFFu)));
+  }
+  __device__ static void store_nearest(__half* p, long long k, C v, int i, float rsc) {
+    p[k] = __float2half_rn(v * (float(1.0 / w_of(i)) * rsc));
   }
 };
 template <> struct Store<__nv_bfloat16> {
@@ -36,8 +53,33 @@ template <> struct Store<__nv_bfloat16> {
   __device__ static C load(const __nv_bfloat16* p, long long k, int i, float sc) {
     return __bfloat162float(p[k]) * (float(w_of(i)) * sc);
   }
-  __device__ static void store(__nv_bfloat16* p, long long k, C v, int i, float sc) {
-    p[k] = __float2bfloat16_rn(v / (float(w_of(i)) * sc));
+  __device__ static void store(__nv_bfloat16* p, long long k, C v, int i, float rsc, uint32_t r) {
+    const float x = v * (float(1.0 / w_of(i)) * rsc);
+    // BF16 is the upper half of the FP32 pattern
+    const uint32_t bits = __float_as_uint(x) + (r & 0xFFFFu);
+    p[k] = __ushort_as_bfloat16(static_cast<unsigned short>(bits >> 16));
+  }
+  __device__ static void store_nearest(__nv_bfloat16* p, long long k, C v, int i, float rsc) {
+    p[k] = __float2bfloat16_rn(v * (float(1.0 / w_of(i)) * rsc));
+  }
+};
+
+// Random bits for the stochastic rounding of the values of one cell: a seed
+// from the cell index and one of the cell's own values (so the draws change
+// from step to step, and the same inputs give the same bits), then a short
+// integer mix per population.  Unused (and compiled away) for FP32 / FP64.
+struct CellDither {
+  uint32_t s;
+  __device__ CellDither(long long cell, float salt) {
+    s = (static_cast<uint32_t>(cell) * 0x9E3779B9u) ^ static_cast<uint32_t>(cell >> 32) ^
+        (__float_as_uint(salt) * 0x85EBCA6Bu);
+  }
+  __device__ uint32_t operator()(int i) const {
+    uint32_t x = s + static_cast<uint32_t>(i) * 0x632BE5ABu;
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    return x;
   }
 };
 

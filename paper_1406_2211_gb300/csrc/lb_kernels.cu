@@ -165,6 +165,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   }
   const C rho = rv<C>(a.rho0) + rd;
   const C inv = C(1) / rho;
+  const CellDither dz(cell, float(rd));
   const C u0x = jx * inv, u0y = jy * inv, u0z = jz * inv;
   C Fx = rv<C>(a.cgg[0]), Fy = rv<C>(a.cgg[1]), Fz = rv<C>(a.cgg[2]);
   if (FORCED) {
@@ -202,7 +203,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       const C q0 = quad_part<C, i>(u0x, u0y, u0z, uu0);
       const C q1 = quad_part<C, i>(u1x, u1y, u1z, uu1);
       const C v = gam * f[i] + C(n_of(i)) * (sm + lin_part<C, i>(qx, qy, qz) + rho * (q1 - gam * q0));
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
     };
     unroll_q(body);
   } else if (COLL == 2) {
@@ -241,7 +242,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
                                 rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) +
                   C(w_of(i)) * post;
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
     };
     unroll_q(out);
   } else {
@@ -266,7 +267,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       constexpr int i = decltype(I)::value;
       const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
                                 rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + post[i];
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.scale16);
+      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
     };
     unroll_q(out);
   }
@@ -334,7 +335,7 @@ __global__ void unstream_kernel(const S* __restrict__ fbar, S* __restrict__ fsta
       const int zz = wrap_int(zt, g.nz);
       v = Store<S>::load(fbar, j * g.qstride + zz * g.plane + (long long)yt * g.pitch + xt, j, a.scale16);
     }
-    Store<S>::store(fstar, j * g.qstride + cell, v, j, a.scale16);
+    Store<S>::store_nearest(fstar, j * g.qstride + cell, v, j, a.rscale16);
   }
 }
 
@@ -350,7 +351,7 @@ __global__ void pull_kernel(const S* __restrict__ fstar, S* __restrict__ fbar, c
   if (g.walls) pull_cell<S, true>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
   else pull_cell<S, false>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Store<S>::store(fbar, i * g.qstride + cell, f[i], i, a.scale16);
+  for (int i = 0; i < Q; ++i) Store<S>::store_nearest(fbar, i * g.qstride + cell, f[i], i, a.rscale16);
 }
 
 // physical density and velocity of every cell (FP64 outputs, dense layout)
@@ -530,7 +531,7 @@ __global__ void init_eq_kernel(const double* __restrict__ rho, const double* __r
     const double cu = cx_of(i) * v0 + cy_of(i) * v1 + cz_of(i) * v2;
     const double w = w_of(i);
     const double dev = w * (r - a.rho0.d) + w * r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-    Store<S>::store(dst, i * g.qstride + cell, typename Store<S>::C(dev), i, a.scale16);
+    Store<S>::store_nearest(dst, i * g.qstride + cell, typename Store<S>::C(dev), i, a.rscale16);
   }
 }
 

@@ -220,6 +220,7 @@ void fill_lb_args(lbc_box* b) {
     a.bb_top[i] = make_real(l.z_walls ? 6.0 * w * l.rho0 * cu_t : 0.0);
   }
   a.scale16 = (float)(l.storage_scale != 0.0 ? l.storage_scale : 1.0);
+  a.rscale16 = (float)(1.0 / (l.storage_scale != 0.0 ? l.storage_scale : 1.0));
 }
 
 bool order2(const lbc_box* b) { return b->cpl.order == 2; }

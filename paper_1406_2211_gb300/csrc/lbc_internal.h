@@ -29,6 +29,7 @@ struct LBArgs {
   const void* Fa; const uint8_t* flag_a;
   const void* Fb; const uint8_t* flag_b;
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
+  float rscale16;         // 1 / scale16
 };
 
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,

@@ -16,7 +16,7 @@ def require_cuda():
 def make_pair(shape, fbar0, coll="bgk", tau=0.8, lam=(0, 0, 0, 0), g=(0, 0, 0),
               walls=False, uw=((0, 0, 0), (0, 0, 0)), storage="f64", kind="none",
               order=2, stencil="trilinear", gamma=1.0, split="base", n=1,
-              parts=None, rho0=1.0, graphs=True):
+              parts=None, rho0=1.0, graphs=True, storage_scale=0.0):
     """(library Box, oracle Sim) with identical inputs.
 
     parts: dict(pos, vel, mass, bonds, bond_k, bond_r0, ext) or None.
@@ -25,7 +25,7 @@ def make_pair(shape, fbar0, coll="bgk", tau=0.8, lam=(0, 0, 0, 0), g=(0, 0, 0),
     nz, ny, nx = shape
     lat = lbc.lattice_desc(nx, ny, nz, collision=coll, tau=tau, mrt_lambda=lam,
                            rho0=rho0, body_force=g, walls=walls, wall_velocity=uw,
-                           storage=storage)
+                           storage=storage, storage_scale=storage_scale)
     cpl = lbc.coupling_desc(kind, order, stencil, gamma=gamma, split=split, substeps=n)
     M = 0 if parts is None else len(parts["pos"])
     B = 0 if parts is None or parts.get("bonds") is None else len(parts["bonds"])
