@@ -17,15 +17,15 @@ namespace lbc {
 template <typename S> struct Store;
 template <> struct Store<double> {
   using C = double;
-  __device__ static C load(const double* p, long long k, int, float) { return __ldg(p + k); }
-  __device__ static void store(double* p, long long k, C v, int, float, uint32_t) { p[k] = v; }
-  __device__ static void store_nearest(double* p, long long k, C v, int, float) { p[k] = v; }
+  template <typename IX> __device__ static C load(const double* p, IX k, int, float) { return __ldg(p + k); }
+  template <typename IX> __device__ static void store(double* p, IX k, C v, int, float, uint32_t) { p[k] = v; }
+  template <typename IX> __device__ static void store_nearest(double* p, IX k, C v, int, float) { p[k] = v; }
 };
 template <> struct Store<float> {
   using C = float;
-  __device__ static C load(const float* p, long long k, int, float) { return __ldg(p + k); }
-  __device__ static void store(float* p, long long k, C v, int, float, uint32_t) { p[k] = v; }
-  __device__ static void store_nearest(float* p, long long k, C v, int, float) { p[k] = v; }
+  template <typename IX> __device__ static C load(const float* p, IX k, int, float) { return __ldg(p + k); }
+  template <typename IX> __device__ static void store(float* p, IX k, C v, int, float, uint32_t) { p[k] = v; }
+  template <typename IX> __device__ static void store_nearest(float* p, IX k, C v, int, float) { p[k] = v; }
 };
 // 16-bit forms store dev / (w_i * scale) so every population uses the same
 // dynamic range, rounded stochastically: random bits are added below the last
@@ -37,29 +37,33 @@ template <> struct Store<float> {
 // random bits, which is unbiased only to within their own spacing.)
 template <> struct Store<__half> {
   using C = float;
-  __device__ static C load(const __half* p, long long k, int i, float sc) {
+  template <typename IX> __device__ static C load(const __half* p, IX k, int i, float sc) {
     return __half2float(p[k]) * (float(w_of(i)) * sc);
   }
-  __device__ static void store(__half* p, long long k, C v, int i, float rsc, uint32_t r) {
+  template <typename IX>
+  __device__ static void store(__half* p, IX k, C v, int i, float rsc, uint32_t r) {
     const float x = v * (float(1.0 / w_of(i)) * rsc);
     p[k] = __float2half_rz(__uint_as_float(__float_as_uint(x) + (r & 0x1FFFu)));
   }
-  __device__ static void store_nearest(__half* p, long long k, C v, int i, float rsc) {
+  template <typename IX>
+  __device__ static void store_nearest(__half* p, IX k, C v, int i, float rsc) {
     p[k] = __float2half_rn(v * (float(1.0 / w_of(i)) * rsc));
   }
 };
 template <> struct Store<__nv_bfloat16> {
   using C = float;
-  __device__ static C load(const __nv_bfloat16* p, long long k, int i, float sc) {
+  template <typename IX> __device__ static C load(const __nv_bfloat16* p, IX k, int i, float sc) {
     return __bfloat162float(p[k]) * (float(w_of(i)) * sc);
   }
-  __device__ static void store(__nv_bfloat16* p, long long k, C v, int i, float rsc, uint32_t r) {
+  template <typename IX>
+  __device__ static void store(__nv_bfloat16* p, IX k, C v, int i, float rsc, uint32_t r) {
     const float x = v * (float(1.0 / w_of(i)) * rsc);
     // BF16 is the upper half of the FP32 pattern
     const uint32_t bits = __float_as_uint(x) + (r & 0xFFFFu);
     p[k] = __ushort_as_bfloat16(static_cast<unsigned short>(bits >> 16));
   }
-  __device__ static void store_nearest(__nv_bfloat16* p, long long k, C v, int i, float rsc) {
+  template <typename IX>
+  __device__ static void store_nearest(__nv_bfloat16* p, IX k, C v, int i, float rsc) {
     p[k] = __float2bfloat16_rn(v * (float(1.0 / w_of(i)) * rsc));
   }
 };
@@ -84,8 +88,10 @@ struct CellDither {
 };
 
 // Pull the 19 post-streaming deviations fbar_i(x, y, z) from the stored
-// pre-streaming array (periodic in x, y; z periodic or bounce-back).
-template <typename S, bool WALLS>
+// pre-streaming array (periodic in x, y; z periodic or bounce-back).  IX is
+// the index type: int where the whole array has fewer than 2^31 elements
+// (fewer integer instructions per load), long long otherwise.
+template <typename S, bool WALLS, typename IX = long long>
 __device__ inline void pull_cell(const S* __restrict__ f, const Geom& g,
                                  const Real* bb_bot, const Real* bb_top,
                                  float sc, int x, int y, int z,
@@ -98,21 +104,25 @@ __device__ inline void pull_cell(const S* __restrict__ f, const Geom& g,
     zm = z == 0 ? g.nz - 1 : zm;
     zp = z == g.nz - 1 ? 0 : zp;
   }
-  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  const IX plane = static_cast<IX>(g.plane), pitch = static_cast<IX>(g.pitch);
+  const IX qs = static_cast<IX>(g.qstride);
+  // row offsets of the source rows z - cz, y - cy
+  const IX rz[3] = {zp * plane, z * plane, zm * plane};     // by cz = -1, 0, +1
+  const IX ry[3] = {yp * pitch, y * pitch, ym * pitch};     // by cy = -1, 0, +1
+  const IX cell = rz[1] + ry[1] + x;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     // source = x - c_i
     const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
-    const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
     const int zs = cz == 0 ? z : (cz > 0 ? zm : zp);
     if (WALLS && cz != 0 && (zs < 0 || zs >= g.nz)) {
       // bounced back at the wall: population opp(i) of this cell, plus the
       // moving-wall momentum term
       const C bb = rv<C>(cz > 0 ? bb_bot[i] : bb_top[i]);
-      out[i] = Store<S>::load(f, opp_of(i) * g.qstride + cell, opp_of(i), sc) + bb;
+      out[i] = Store<S>::load(f, static_cast<IX>(opp_of(i)) * qs + cell, opp_of(i), sc) + bb;
     } else {
-      out[i] = Store<S>::load(f, i * g.qstride + zs * g.plane + (long long)ys * g.pitch + xs, i, sc);
+      out[i] = Store<S>::load(f, static_cast<IX>(i) * qs + rz[cz + 1] + ry[cy + 1] + xs, i, sc);
     }
   }
 }

@@ -142,7 +142,18 @@ __device__ inline void back_all(const C (&m)[Q], C (&post)[Q]) {
   }
 }
 
-template <typename S, int COLL, bool WALLS, bool FORCED>
+// Opposite populations i, opp(i) = i + 1 (i odd) share every term that is
+// even in c_i (density, quadratic and stress parts) and differ in the sign
+// of the odd ones, so the output is formed per pair as E +- O.
+template <int P = 0, typename F>
+__device__ inline void unroll_pairs(F&& f) {
+  if constexpr (P < 9) {
+    f(IC<2 * P + 1>{});
+    unroll_pairs<P + 1>(f);
+  }
+}
+
+template <typename S, int COLL, bool WALLS, bool FORCED, typename IX>
 __global__ void __launch_bounds__(256, 5)
 lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
   using C = typename Store<S>::C;
@@ -150,10 +161,11 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= g.nx) return;
-  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  const IX qs = static_cast<IX>(g.qstride);
+  const IX cell = static_cast<IX>(z) * static_cast<IX>(g.plane) + static_cast<IX>(y) * g.pitch + x;
 
   C f[Q];
-  pull_cell<S, WALLS>(fin, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  pull_cell<S, WALLS, IX>(fin, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
 
   C rd = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
@@ -175,20 +187,21 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     if (Fa && a.flag_a[t]) {
       const C ca = rv<C>(a.ca);
       Fx += ca * Fa[cell];
-      Fy += ca * Fa[g.qstride + cell];
-      Fz += ca * Fa[2 * g.qstride + cell];
+      Fy += ca * Fa[qs + cell];
+      Fz += ca * Fa[2 * qs + cell];
     }
     if (Fb && a.flag_b[t]) {
       const C cb = rv<C>(a.cb);
       Fx += cb * Fb[cell];
-      Fy += cb * Fb[g.qstride + cell];
-      Fz += cb * Fb[2 * g.qstride + cell];
+      Fy += cb * Fb[qs + cell];
+      Fz += cb * Fb[2 * qs + cell];
     }
   }
   const C u1x = u0x + Fx * inv, u1y = u0y + Fy * inv, u1z = u0z + Fz * inv;
 
   const C uu0 = div_by<C, 24>(u0x * u0x + u0y * u0y + u0z * u0z);
   const C uu1 = div_by<C, 24>(u1x * u1x + u1y * u1y + u1z * u1z);
+  auto put = [&](int i, C v) { Store<S>::store(fout, static_cast<IX>(i) * qs + cell, v, i, a.rscale16, dz(i)); };
 
   if (COLL == 0) {
     // f*_i = gamma fbar_i + n_i [ (1-gamma) rd/36 + c_i.((1-gamma) j + F)/12
@@ -198,14 +211,20 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     const C sm = div_by<C, 36>(omg * rd);
     const C qx = div_by<C, 12>(omg * jx + Fx), qy = div_by<C, 12>(omg * jy + Fy),
             qz = div_by<C, 12>(omg * jz + Fz);
-    auto body = [&](auto I) {
+    {
+      const C q0 = quad_part<C, 0>(u0x, u0y, u0z, uu0);
+      const C q1 = quad_part<C, 0>(u1x, u1y, u1z, uu1);
+      put(0, gam * f[0] + C(n_of(0)) * (sm + rho * (q1 - gam * q0)));
+    }
+    unroll_pairs([&](auto I) {
       constexpr int i = decltype(I)::value;
       const C q0 = quad_part<C, i>(u0x, u0y, u0z, uu0);
       const C q1 = quad_part<C, i>(u1x, u1y, u1z, uu1);
-      const C v = gam * f[i] + C(n_of(i)) * (sm + lin_part<C, i>(qx, qy, qz) + rho * (q1 - gam * q0));
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
-    };
-    unroll_q(body);
+      const C E = C(n_of(i)) * (sm + rho * (q1 - gam * q0));
+      const C O = C(n_of(i)) * lin_part<C, i>(qx, qy, qz);
+      put(i, gam * f[i] + (E + O));
+      put(i + 1, gam * f[i + 1] + (E - O));
+    });
   } else if (COLL == 2) {
     // MRT with both ghost groups fully relaxed (their eigenvalue 1 - lambda
     // is 0): only the bulk and shear moments 4..9 carry non-equilibrium
@@ -230,7 +249,9 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     m[9] = nxz * (gs * C(1.0 / mrt_b(9)));
     const C md = div_by<C, 36>(rd);
     const C j1x = div_by<C, 12>(jx + Fx), j1y = div_by<C, 12>(jy + Fy), j1z = div_by<C, 12>(jz + Fz);
-    auto out = [&](auto I) {
+    // the even part of population i: equilibrium density and quadratic
+    // terms plus w_i sum_k e_ki m_k (k = 4..9 are even in c)
+    auto even = [&](auto I) {
       constexpr int i = decltype(I)::value;
       C post = C(0);
       if constexpr (mrt_e(4, i) != 0) post += C(mrt_e(4, i)) * m[4];
@@ -239,12 +260,16 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       if constexpr (mrt_e(7, i) != 0) post += C(mrt_e(7, i)) * m[7];
       if constexpr (mrt_e(8, i) != 0) post += C(mrt_e(8, i)) * m[8];
       if constexpr (mrt_e(9, i) != 0) post += C(mrt_e(9, i)) * m[9];
-      const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
-                                rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) +
-                  C(w_of(i)) * post;
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
+      return C(n_of(i)) * (md + rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + C(w_of(i)) * post;
     };
-    unroll_q(out);
+    put(0, even(IC<0>{}));
+    unroll_pairs([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const C E = even(I);
+      const C O = C(n_of(i)) * lin_part<C, i>(j1x, j1y, j1z);
+      put(i, E + O);
+      put(i + 1, E - O);
+    });
   } else {
     // neq_i = fbar_i - f_i^eq(rho, u0); relax per moment; add f^eq(rho, u1)
     const C md = div_by<C, 36>(rd);
@@ -267,7 +292,7 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       constexpr int i = decltype(I)::value;
       const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
                                 rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + post[i];
-      Store<S>::store(fout, i * g.qstride + cell, v, i, a.rscale16, dz(i));
+      put(i, v);
     };
     unroll_q(out);
   }
@@ -287,7 +312,13 @@ static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream
   const bool forced = a.Fa != nullptr || a.Fb != nullptr;
   const S* in = static_cast<const S*>(fin);
   S* out = static_cast<S*>(fout);
-#define LBC_LAUNCH(COLL, W, F) lb_step_kernel<S, COLL, W, F><<<grid, bx, 0, s>>>(in, out, a)
+  // 32-bit indices where all Q populations fit below 2^31 elements
+  const bool i32 = (long long)Q * a.g.qstride < (1LL << 31);
+#define LBC_LAUNCH(COLL, W, F)                                                   \
+  do {                                                                           \
+    if (i32) lb_step_kernel<S, COLL, W, F, int><<<grid, bx, 0, s>>>(in, out, a); \
+    else lb_step_kernel<S, COLL, W, F, long long><<<grid, bx, 0, s>>>(in, out, a); \
+  } while (0)
   if (a.collision == 0) {
     if (a.g.walls) { if (forced) LBC_LAUNCH(0, true, true); else LBC_LAUNCH(0, true, false); }
     else { if (forced) LBC_LAUNCH(0, false, true); else LBC_LAUNCH(0, false, false); }
