@@ -296,6 +296,65 @@ def run_gpu(args, rank, world, local_rank):
     return line
 
 
+# ------------------------------------------------------------------ serving
+def serving_jobs(njobs, seed, step_scale, rate=None):
+    """A bounded sample of the serving ensemble: cubic periodic boxes of edge
+    log-uniform in [32, 128], 1-5000 force-coupled particles (gamma uniform in
+    [0.5, 10]), FP32 or FP16-deviation storage (50/50), steps uniform in
+    [1000, 20000] divided by step_scale, Poisson arrivals at `rate` jobs/s
+    (all at t = 0 if None)."""
+    import numpy as np
+    import synth
+    from paper_1406_2211_gb300.serve import Job
+    lo, hi = 1000 // step_scale, 20000 // step_scale
+    specs = synth.ensemble_jobs(njobs, seed=seed, steps_range=(lo, hi), rate=rate)
+    jobs = []
+    for i, sp in enumerate(specs):
+        rng = np.random.default_rng(sp["seed"])
+        L, M = sp["edge"], sp["nparticles"]
+        spec = dict(edge=L, gamma=sp["gamma"], storage=sp["storage"],
+                    pos=rng.uniform(0.0, L, (M, 3)), vel=np.zeros((M, 3)))
+        jobs.append(Job(i, spec, sp["arrival"], sp["steps"], L ** 3))
+    return jobs
+
+
+def run_serving(args):
+    """Continuous batching of the ensemble sample: first with every job
+    queued at t = 0 (capacity), then with Poisson arrivals at 0.8 x that
+    capacity (latency).  Returns the serving summary."""
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    from paper_1406_2211_gb300.serve import BoxFactory, JobServer, summary
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    slots = 32
+
+    def serve(jobs):
+        batch = lbc.Batch(slots)
+        srv = JobServer(BoxFactory(), batch, budget, slots, chunk_steps=50,
+                        sync=torch.cuda.synchronize)
+        done = srv.run(jobs)
+        out = summary(done, srv.elapsed)
+        out["peak_active"] = srv.peak_active
+        out["peak_bytes"] = srv.peak_bytes
+        batch.close()
+        torch.cuda.empty_cache()
+        return out
+
+    n = args.serve_jobs
+    sat = serve(serving_jobs(n, 12345, 20))
+    rate = 0.8 * sat["jobs_per_s"]
+    lat = serve(serving_jobs(n, 12345, 20, rate=rate))
+    return {"jobs": n, "unit": "jobs/s", "value": lat["jobs_per_s"], "mlups": lat["mlups"],
+            "p50_latency_s": lat["p50_latency_s"], "p99_latency_s": lat["p99_latency_s"],
+            "offered_rate_jobs_per_s": rate, "offered_load": 0.8,
+            "capacity_jobs_per_s": sat["jobs_per_s"], "capacity_mlups": sat["mlups"],
+            "peak_active": lat["peak_active"], "slots": slots, "memory_budget_bytes": budget,
+            "sample": "%d jobs of the 2000-job ensemble (same distributions), steps / 20 "
+                      "(50-1000), seed 12345; arrivals Poisson at 0.8 x the capacity "
+                      "measured with all jobs queued at t = 0" % n}
+
+
 # ------------------------------------------------------------------ CPU arm
 def oracle_sample(max_seconds, min_steps=2, max_steps=None):
     """The FP64 oracle on a bounded sample of the workload: the 256^3 box cut
@@ -377,6 +436,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the ensemble serving measurement")
+    ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the 16-bit storage forms of the same step")
     # box edge / SCALE and particle count / SCALE^3 at the same densities: the
@@ -406,6 +468,8 @@ def main():
         cpu = cpu_baseline_subprocess(args.cpu_seconds)
     line = run_gpu(args, rank, world, local_rank)
     line["cpu_baseline"] = cpu
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

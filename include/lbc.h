@@ -230,6 +230,67 @@ int64_t lbc_box_launches_per_step(const lbc_box* box);
 /* Bytes of one population array (for bandwidth accounting). */
 size_t lbc_box_population_bytes(const lbc_box* box);
 
+/* ------------------------------------------------------------ batching
+ * A batch advances many independent boxes together: per time step, the
+ * particle work before the LB step of every member runs concurrently (one
+ * stream per member), then one batched LB launch per group of members that
+ * share storage, collision kind, walls and forcing covers all their cells
+ * (box table in device memory, one x-row per block), then the particle work
+ * after the LB step.  Two such steps are captured once in a CUDA graph and
+ * replayed; the graph is recaptured when members join or leave.  This is
+ * the continuous batching behind a serving loop: members are admitted while
+ * others are in flight and leave when their step budget is spent.  The
+ * paper has no counterpart (it describes one box).
+ *
+ * Results of a member do not depend on the other members: the same kernels
+ * run with the same per-box arguments, so a box advanced in a batch matches
+ * the same box advanced in a batch of its own bit for bit.
+ *
+ * Limits: x-rows of at most LBC_BATCH_MAX_NX cells; boxes must have been
+ * created without LBC_OPT_TIMING.  The batch owns no device memory: the
+ * caller passes an arena of lbc_batch_bytes_required(max_boxes) bytes. */
+typedef struct lbc_batch lbc_batch;
+#define LBC_BATCH_MAX_NX 128
+
+/* Device bytes the batch needs for its box tables (max_boxes members). */
+size_t lbc_batch_bytes_required(int32_t max_boxes);
+
+/* Create a batch of up to max_boxes members using the caller's device arena
+ * (256-byte aligned, at least lbc_batch_bytes_required(max_boxes) bytes;
+ * the caller keeps ownership and frees it after lbc_batch_destroy()).
+ * Errors: LBC_ERR_ARG (max_boxes < 1 or > 1024, NULL pointers),
+ * LBC_ERR_OOM (arena too small), LBC_ERR_CUDA. */
+lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_bytes,
+                            lbc_batch** out);
+
+/* Admit a box with a budget of `steps` time steps (>= 1).  Errors:
+ * LBC_ERR_OOM (no free slot), LBC_ERR_ARG (NULL, steps < 1, nx >
+ * LBC_BATCH_MAX_NX), LBC_ERR_STATE (the box is in a batch already or has
+ * LBC_OPT_TIMING set). */
+lbc_status lbc_batch_add(lbc_batch* batch, lbc_box* box, int64_t steps);
+
+/* Remove a member before its budget is spent (its state is that of the
+ * last completed step).  LBC_ERR_ARG if the box is not a member. */
+lbc_status lbc_batch_remove(lbc_batch* batch, lbc_box* box);
+
+/* Steps left in a member's budget (LBC_ERR_ARG if not a member). */
+lbc_status lbc_batch_remaining(const lbc_batch* batch, const lbc_box* box, int64_t* steps);
+
+/* Advance every member by k = min(max_steps, smallest remaining budget)
+ * steps, enqueued on `stream` (asynchronous).  Members whose budget reaches
+ * zero leave the batch and are written to finished[0 .. *nfinished) (room
+ * for max_boxes entries); their results can then be read with the box
+ * getters.  *steps_done receives k (0 for an empty batch). */
+lbc_status lbc_batch_advance(lbc_batch* batch, int64_t max_steps, void* stream,
+                             lbc_box** finished, int32_t* nfinished, int64_t* steps_done);
+
+/* Number of members and the kernel launches one batched step enqueues. */
+int32_t lbc_batch_size(const lbc_batch* batch);
+int64_t lbc_batch_launches_per_step(const lbc_batch* batch);
+
+/* Free the batch object (members are released, not destroyed). */
+lbc_status lbc_batch_destroy(lbc_batch* batch);
+
 /* Total mass and momentum of a post-streaming population array in device
  * memory, for callers that cannot allocate: it calls no cudaMalloc and needs
  * no arena, because its scratch is a fixed file-scope device array of

@@ -153,14 +153,12 @@ __device__ inline void unroll_pairs(F&& f) {
   }
 }
 
+// one cell (x, y, z) of the fused step
 template <typename S, int COLL, bool WALLS, bool FORCED, typename IX>
-__global__ void __launch_bounds__(256, 5)
-lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
+__device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict__ fout,
+                                        const LBArgs& a, int x, int y, int z) {
   using C = typename Store<S>::C;
   const Geom& g = a.g;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= g.nx) return;
   const IX qs = static_cast<IX>(g.qstride);
   const IX cell = static_cast<IX>(z) * static_cast<IX>(g.plane) + static_cast<IX>(y) * g.pitch + x;
 
@@ -298,6 +296,39 @@ lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   }
 }
 
+template <typename S, int COLL, bool WALLS, bool FORCED, typename IX>
+__global__ void __launch_bounds__(256, 5)
+lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.g.nx) return;
+  lb_cell<S, COLL, WALLS, FORCED, IX>(fin, fout, a, x, blockIdx.y, blockIdx.z);
+}
+
+// Many boxes in one launch: block b advances one x-row of the box whose row
+// range [row0, row0 + ny nz) contains b (boxes of any size, rows of at most
+// blockDim.x cells).  The box table lives in device memory.
+template <typename S, int COLL, bool WALLS, bool FORCED, typename IX>
+__global__ void __launch_bounds__(128)
+lb_batch_kernel(const BoxEntry* __restrict__ boxes, int nboxes) {
+  __shared__ int sbox;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nboxes - 1;                 // last box with row0 <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (boxes[mid].row0 <= (long long)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    sbox = lo;
+  }
+  __syncthreads();
+  const BoxEntry& e = boxes[sbox];
+  const long long r = (long long)blockIdx.x - e.row0;
+  const int x = threadIdx.x;
+  if (x >= e.a.g.nx) return;
+  const int y = static_cast<int>(r % e.a.g.ny), z = static_cast<int>(r / e.a.g.ny);
+  lb_cell<S, COLL, WALLS, FORCED, IX>(static_cast<const S*>(e.fin), static_cast<S*>(e.fout), e.a,
+                                      x, y, z);
+}
+
 static dim3 cell_grid(const Geom& g, int* bx) {
   int b = ((g.nx + 31) / 32) * 32;
   if (b > 256) b = 256;
@@ -330,6 +361,40 @@ static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream
     else { if (forced) LBC_LAUNCH(1, false, true); else LBC_LAUNCH(1, false, false); }
   }
 #undef LBC_LAUNCH
+}
+
+template <typename S>
+static void lb_batch_dispatch(const BoxEntry* boxes, int nboxes, long long rows, int coll, bool walls,
+                              bool forced, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>(rows));
+#define LBC_BATCH(COLL, W, F) lb_batch_kernel<S, COLL, W, F, int><<<grid, 128, 0, s>>>(boxes, nboxes)
+  if (coll == 0) {
+    if (walls) { if (forced) LBC_BATCH(0, true, true); else LBC_BATCH(0, true, false); }
+    else { if (forced) LBC_BATCH(0, false, true); else LBC_BATCH(0, false, false); }
+  } else if (coll == 2) {
+    if (walls) { if (forced) LBC_BATCH(2, true, true); else LBC_BATCH(2, true, false); }
+    else { if (forced) LBC_BATCH(2, false, true); else LBC_BATCH(2, false, false); }
+  } else {
+    if (walls) { if (forced) LBC_BATCH(1, true, true); else LBC_BATCH(1, true, false); }
+    else { if (forced) LBC_BATCH(1, false, true); else LBC_BATCH(1, false, false); }
+  }
+#undef LBC_BATCH
+}
+
+int lb_collision_variant(const LBArgs& a) {
+  if (a.collision == 0) return 0;
+  return (a.gamma_k[2].d == 0.0 && a.gamma_k[3].d == 0.0) ? 2 : 1;
+}
+
+void launch_lb_batch(int storage, const BoxEntry* boxes, int nboxes, long long rows, int coll,
+                     bool walls, bool forced, cudaStream_t s) {
+  if (nboxes <= 0 || rows <= 0) return;
+  switch (storage) {
+    case ST_F64: lb_batch_dispatch<double>(boxes, nboxes, rows, coll, walls, forced, s); break;
+    case ST_F32: lb_batch_dispatch<float>(boxes, nboxes, rows, coll, walls, forced, s); break;
+    case ST_F16: lb_batch_dispatch<__half>(boxes, nboxes, rows, coll, walls, forced, s); break;
+    default: lb_batch_dispatch<__nv_bfloat16>(boxes, nboxes, rows, coll, walls, forced, s); break;
+  }
 }
 
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s) {

@@ -138,6 +138,8 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
 
 }  // namespace
 
+struct lbc_batch;
+
 struct lbc_box {
   lbc_lattice_desc lat;
   lbc_coupling_desc cpl;
@@ -164,6 +166,8 @@ struct lbc_box {
   lbc_status status;
   LBArgs lb;        // constant part of the LB arguments
   int64_t launches;
+  BoxEntry deferred;   // the LB step recorded by a phase-1 pass (batched launch)
+  lbc_batch* batch;    // the batch this box belongs to, or null
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
   void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
@@ -241,6 +245,11 @@ struct Plan {
   lbc_box* b;
   cudaStream_t s;
   int64_t n = 0;   // launches enqueued
+  // 0: the whole step; 1: the part before the LB step, whose arguments are
+  // recorded in b->deferred for a batched launch; 2: the part after it
+  int phase = 0;
+  bool after_lb = false;
+  bool on() const { return phase == 0 || (phase == 1) != after_lb; }
 
   void lb(const void* Fa, const void* Fb, double ca, double cb, double cg) {
     LBArgs a = b->lb;
@@ -248,6 +257,17 @@ struct Plan {
     a.Fb = Fb; a.flag_b = Fb ? (Fb == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.ca = make_real(ca); a.cb = make_real(cb);
     for (int c = 0; c < 3; ++c) a.cgg[c] = make_real(cg * b->lat.body_force[c]);
+    if (phase != 0) {
+      if (phase == 1) {
+        b->deferred.a = a;
+        b->deferred.fin = b->pop(b->cur);
+        b->deferred.fout = b->pop(1 - b->cur);
+        b->deferred.row0 = 0;
+        b->cur = 1 - b->cur;
+      }
+      after_lb = true;
+      return;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->timing_cap > 0) {
       if (b->capturing) {
@@ -273,6 +293,7 @@ struct Plan {
   // buffer, output the other one (flips pc) unless positions are not written
   void drift(double pre, double kick, double post, bool force, bool key, bool write = true,
              const double* pos_in = nullptr, double pre0 = 0.0) {
+    if (!on()) return;
     DriftArgs d{};
     d.dt_pre0 = pre0;
     d.dt_pre = pre; d.dt_kick = kick; d.dt_post = post;
@@ -298,6 +319,7 @@ struct Plan {
   }
 
   void sort() {
+    if (!on()) return;
     const int kb = key_bits(b->L.ntiles);
     launch_sort(b->M, kb, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
                 b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), s);
@@ -350,11 +372,13 @@ struct Plan {
   }
 
   void gather(const GatherArgs& a) {
+    if (!on()) return;
     launch_gather(part_args(b), a, s);
     ++n;
   }
 
   void spread(int out, bool carry) {
+    if (!on()) return;
     SpreadArgs a{};
     a.rec = b->arena + b->L.off_rec;
     a.reach = reinterpret_cast<const short4*>(b->arena + b->L.off_reach);
@@ -375,8 +399,9 @@ struct Plan {
 };
 
 // One time step of the configured scheme (h = 1).
-void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
+void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) {
   Plan P{b, s};
+  P.phase = phase;
   const double h = 1.0;
   const int kind = b->cpl.kind;
   if (!particles(b)) {
@@ -385,7 +410,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
     // force (set by lbc_box_set_pending_force) is applied once and cleared.
     if (b->L.has_particles && order2(b)) {
       P.lb(b->F(b->ia), nullptr, 0.5 * h, 0.0, h);
-      cudaMemsetAsync(b->flag(b->ia), 0, b->L.ntiles, s);
+      if (P.on()) cudaMemsetAsync(b->flag(b->ia), 0, b->L.ntiles, s);
     } else {
       P.lb(nullptr, nullptr, 0.0, 0.0, h);
     }
@@ -412,7 +437,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches) {
       a.mode = GM_IBM_FINAL; a.s = make_real(0.5 * h);
       P.fields(a, ib, 0.5 * h, -1, 0.0, 0.5 * h);
       P.gather(a);
-      b->ia = ib;
+      if (P.on()) b->ia = ib;
     } else {
       P.drift(0.0, 0.0, 0.0, true, true, false);
       P.sort();
@@ -773,6 +798,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->lb_in_capture = 0;
   b->status = LBC_OK;
   b->launches = 0;
+  b->batch = nullptr;
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -802,6 +828,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
 
 lbc_status lbc_box_destroy(lbc_box* b) {
   if (!b) return LBC_ERR_ARG;
+  if (b->batch) lbc_batch_remove(b->batch, b);
   reset_graphs(b);
   free_timing(b);
   delete b;
@@ -810,6 +837,7 @@ lbc_status lbc_box_destroy(lbc_box* b) {
 
 lbc_status lbc_box_init_equilibrium(lbc_box* b, double rho, const double u[3], void* stream) {
   if (!b || !(rho > 0.0)) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // members change only between batches
   cudaStream_t s = S(stream);
   void* spare = b->pop(1 - b->cur);
   launch_init_eq(b->lat.storage, nullptr, nullptr, spare, b->lb, 1, rho, u, s);
@@ -822,6 +850,7 @@ lbc_status lbc_box_init_equilibrium(lbc_box* b, double rho, const double u[3], v
 
 lbc_status lbc_box_set_fields(lbc_box* b, const double* rho, const double* u, void* stream) {
   if (!b || !rho || !u) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // members change only between batches
   cudaStream_t s = S(stream);
   const Geom& g = b->L.g;
   const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -843,6 +872,7 @@ lbc_status lbc_box_set_fields(lbc_box* b, const double* rho, const double* u, vo
 
 lbc_status lbc_box_set_populations(lbc_box* b, const double* f, void* stream) {
   if (!b || !f) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // members change only between batches
   cudaStream_t s = S(stream);
   lbc_status st;
   switch (b->lat.storage) {
@@ -870,6 +900,7 @@ lbc_status lbc_box_get_populations(lbc_box* b, double* f, void* stream) {
 
 lbc_status lbc_box_set_pending_force(lbc_box* b, const double* Fa, void* stream) {
   if (!b) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // members change only between batches
   if (!b->L.has_particles) return Fa ? LBC_ERR_STATE : LBC_OK;
   cudaStream_t s = S(stream);
   if (!Fa) return clear_pending(b, s);
@@ -898,6 +929,7 @@ lbc_status lbc_box_set_pending_force(lbc_box* b, const double* Fa, void* stream)
 
 lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* stream) {
   if (!b || !p || p->n < 0 || p->nbonds < 0) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // members change only between batches
   if (p->n > b->maxM || p->nbonds > b->maxB) return LBC_ERR_OOM;
   if (p->n > 0 && !p->pos) return LBC_ERR_ARG;
   if (p->nbonds > 0 && (!p->bond_ij || !p->bond_k || !p->bond_r0)) return LBC_ERR_ARG;
@@ -986,6 +1018,7 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
 
 lbc_status lbc_box_step(lbc_box* b, int64_t nsteps, void* stream) {
   if (!b || nsteps < 0) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;     // a member advances with its batch
   if (b->status != LBC_OK) return b->status;
   return run_steps(b, nsteps, S(stream));
 }
@@ -1059,6 +1092,7 @@ lbc_status lbc_box_status(const lbc_box* b) { return b ? b->status : LBC_ERR_ARG
 
 lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
   if (!b) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;
   if (option == LBC_OPT_GRAPHS) {
     b->use_graphs = value ? 1 : 0;
     reset_graphs(b);
@@ -1102,5 +1136,330 @@ int64_t lbc_box_launches_per_step(const lbc_box* b) {
 }
 
 size_t lbc_box_population_bytes(const lbc_box* b) { return b ? b->L.pop_bytes : 0; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batching
+// Members advance together: per batched step, the phase-1 part of every
+// member's step (particle work before its LB step) runs on the member's own
+// stream, the LB steps of all members run as one launch per group (storage,
+// collision variant, walls, forcing) over a box table, then the phase-2
+// parts run on the member streams again.  Two batched steps are captured as
+// one CUDA graph per step parity and replayed while the membership is
+// unchanged.
+struct lbc_batch {
+  struct Member {
+    lbc_box* box;
+    int64_t remaining;
+  };
+  int max_boxes;
+  BoxEntry* tables;                 // 5 regions of max_boxes entries (device)
+  std::vector<Member> members;
+  std::vector<cudaStream_t> streams;     // one per slot
+  std::vector<cudaEvent_t> events;       // one per slot
+  cudaEvent_t fork[2];
+  cudaGraphExec_t graph[2];
+  cudaGraph_t tgraph[2];
+  cudaStream_t graph_stream[2];
+  int parity;        // toggled every batched step
+  bool steady;       // a batched step ran since the membership last changed
+  int64_t launches;  // kernel launches of one batched step
+};
+
+namespace {
+
+constexpr int kBatchRegions = 5;   // graph[p] steps 1, 2 use regions 2p, 2p + 1; eager: 4
+
+size_t batch_table_bytes(int max_boxes) {
+  return (size_t)kBatchRegions * (size_t)max_boxes * sizeof(BoxEntry);
+}
+
+void batch_reset_graphs(lbc_batch* B) {
+  for (int k = 0; k < 2; ++k) {
+    if (B->graph[k]) cudaGraphExecDestroy(B->graph[k]);
+    if (B->tgraph[k]) cudaGraphDestroy(B->tgraph[k]);
+    B->graph[k] = nullptr;
+    B->tgraph[k] = nullptr;
+    B->graph_stream[k] = nullptr;
+  }
+  B->steady = false;
+}
+
+// Enqueue one batched step on `main`.  The box table of the LB launches is
+// built in `host` and must be on the device at `dev` before the launches
+// run: with copy = true it is copied on `main` here (eager steps); during
+// capture the caller copies it after the capture ends.
+lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vector<BoxEntry>& host,
+                      bool copy, int64_t* launches) {
+  const int n = (int)B->members.size();
+  int64_t l = 0;
+  CK(cudaEventRecord(B->fork[0], main));
+  for (int j = 0; j < n; ++j) {
+    cudaStream_t sj = B->streams[j];
+    CK(cudaStreamWaitEvent(sj, B->fork[0], 0));
+    int64_t lj = 0;
+    enqueue_step(B->members[j].box, sj, &lj, 1);
+    l += lj;
+    CK(cudaEventRecord(B->events[j], sj));
+    CK(cudaStreamWaitEvent(main, B->events[j], 0));
+  }
+  // group the recorded LB steps; rows are numbered per group in table order
+  struct Key {
+    int storage, coll, walls, forced;
+    bool operator==(const Key& o) const {
+      return storage == o.storage && coll == o.coll && walls == o.walls && forced == o.forced;
+    }
+  };
+  std::vector<Key> keys;
+  std::vector<std::vector<int>> groups;
+  for (int j = 0; j < n; ++j) {
+    const lbc_box* b = B->members[j].box;
+    const BoxEntry& e = b->deferred;
+    const Key k{b->lat.storage, lb_collision_variant(e.a), e.a.g.walls,
+                (e.a.Fa != nullptr || e.a.Fb != nullptr) ? 1 : 0};
+    size_t gi = 0;
+    while (gi < keys.size() && !(keys[gi] == k)) ++gi;
+    if (gi == keys.size()) { keys.push_back(k); groups.emplace_back(); }
+    groups[gi].push_back(j);
+  }
+  host.clear();
+  std::vector<std::pair<size_t, long long>> spans;   // (first entry, rows) per group
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const size_t first = host.size();
+    long long rows = 0;
+    for (int j : groups[gi]) {
+      BoxEntry e = B->members[j].box->deferred;
+      e.row0 = rows;
+      rows += (long long)e.a.g.ny * e.a.g.nz;
+      host.push_back(e);
+    }
+    spans.emplace_back(first, rows);
+  }
+  if (copy && !host.empty())
+    CK(cudaMemcpyAsync(dev, host.data(), host.size() * sizeof(BoxEntry), cudaMemcpyHostToDevice, main));
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    launch_lb_batch(keys[gi].storage, dev + spans[gi].first, (int)groups[gi].size(),
+                    spans[gi].second, keys[gi].coll, keys[gi].walls != 0, keys[gi].forced != 0, main);
+    ++l;
+  }
+  CK(cudaEventRecord(B->fork[1], main));
+  for (int j = 0; j < n; ++j) {
+    cudaStream_t sj = B->streams[j];
+    CK(cudaStreamWaitEvent(sj, B->fork[1], 0));
+    int64_t lj = 0;
+    enqueue_step(B->members[j].box, sj, &lj, 2);
+    l += lj;
+    CK(cudaEventRecord(B->events[j], sj));
+    CK(cudaStreamWaitEvent(main, B->events[j], 0));
+  }
+  B->parity ^= 1;
+  *launches = l;
+  return last_launch();
+}
+
+// capture two batched steps starting at the current parity
+lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
+  const int par = B->parity;
+  if (B->graph[par]) {
+    cudaGraphExecDestroy(B->graph[par]);
+    cudaGraphDestroy(B->tgraph[par]);
+    B->graph[par] = nullptr;
+    B->tgraph[par] = nullptr;
+  }
+  cudaStream_t cs = s;
+  bool own = false;
+  if (cs == nullptr || cs == cudaStreamLegacy || cs == cudaStreamPerThread) {
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    own = true;
+  }
+  struct Saved { int cur, ia, pc; bool sorted; };
+  std::vector<Saved> saved;
+  for (const auto& m : B->members)
+    saved.push_back({m.box->cur, m.box->ia, m.box->pc, m.box->sorted});
+  std::vector<BoxEntry> host[2];
+  int64_t l = 0;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  BoxEntry* region0 = B->tables + (size_t)(2 * par) * B->max_boxes;
+  BoxEntry* region1 = B->tables + (size_t)(2 * par + 1) * B->max_boxes;
+  lbc_status st1 = batch_step(B, cs, region0, host[0], false, &l);
+  lbc_status st2 = batch_step(B, cs, region1, host[1], false, &l);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (own) cudaStreamDestroy(cs);
+  if (st1 != LBC_OK || st2 != LBC_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st1 != LBC_OK ? st1 : (st2 != LBC_OK ? st2 : LBC_ERR_CUDA);
+  }
+  for (size_t j = 0; j < B->members.size(); ++j) {
+    const lbc_box* b = B->members[j].box;
+    const Saved& v = saved[j];
+    if (b->cur != v.cur || b->ia != v.ia || b->pc != v.pc || b->sorted != v.sorted) {
+      cudaGraphDestroy(graph);
+      return LBC_ERR_STATE;
+    }
+  }
+  // the box tables the captured launches read
+  CK(cudaMemcpy(region0, host[0].data(), host[0].size() * sizeof(BoxEntry), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(region1, host[1].data(), host[1].size() * sizeof(BoxEntry), cudaMemcpyHostToDevice));
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return LBC_ERR_CUDA;
+  }
+  B->graph[par] = exec;
+  B->tgraph[par] = graph;
+  B->graph_stream[par] = s;
+  return LBC_OK;
+}
+
+int batch_find(const lbc_batch* B, const lbc_box* b) {
+  for (size_t j = 0; j < B->members.size(); ++j)
+    if (B->members[j].box == b) return (int)j;
+  return -1;
+}
+
+void batch_drop(lbc_batch* B, int j) {
+  B->members[j].box->batch = nullptr;
+  B->members.erase(B->members.begin() + j);
+  batch_reset_graphs(B);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbc_batch_bytes_required(int32_t max_boxes) {
+  if (max_boxes < 1 || max_boxes > 1024) return 0;
+  return batch_table_bytes(max_boxes);
+}
+
+lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_bytes,
+                            lbc_batch** out) {
+  if (!out || max_boxes < 1 || max_boxes > 1024 || !arena_dev ||
+      (reinterpret_cast<uintptr_t>(arena_dev) & 255u))
+    return LBC_ERR_ARG;
+  if (arena_bytes < batch_table_bytes(max_boxes)) return LBC_ERR_OOM;
+  lbc_batch* B = new (std::nothrow) lbc_batch();
+  if (!B) return LBC_ERR_OOM;
+  B->max_boxes = max_boxes;
+  B->tables = static_cast<BoxEntry*>(arena_dev);
+  B->parity = 0;
+  B->steady = false;
+  B->launches = 0;
+  for (int k = 0; k < 2; ++k) {
+    B->graph[k] = nullptr;
+    B->tgraph[k] = nullptr;
+    B->graph_stream[k] = nullptr;
+    B->fork[k] = nullptr;
+  }
+  bool ok = cudaEventCreateWithFlags(&B->fork[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->fork[1], cudaEventDisableTiming) == cudaSuccess;
+  B->streams.assign(max_boxes, nullptr);
+  B->events.assign(max_boxes, nullptr);
+  for (int j = 0; ok && j < max_boxes; ++j)
+    ok = cudaStreamCreateWithFlags(&B->streams[j], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&B->events[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    lbc_batch_destroy(B);
+    return LBC_ERR_CUDA;
+  }
+  *out = B;
+  return LBC_OK;
+}
+
+lbc_status lbc_batch_add(lbc_batch* B, lbc_box* b, int64_t steps) {
+  if (!B || !b || steps < 1) return LBC_ERR_ARG;
+  if (b->L.g.nx > LBC_BATCH_MAX_NX) return LBC_ERR_ARG;
+  if (b->batch != nullptr || b->timing_cap > 0) return LBC_ERR_STATE;
+  if ((int)B->members.size() >= B->max_boxes) return LBC_ERR_OOM;
+  if (b->status != LBC_OK) return b->status;
+  B->members.push_back({b, steps});
+  b->batch = B;
+  batch_reset_graphs(B);
+  return LBC_OK;
+}
+
+lbc_status lbc_batch_remove(lbc_batch* B, lbc_box* b) {
+  if (!B || !b) return LBC_ERR_ARG;
+  const int j = batch_find(B, b);
+  if (j < 0) return LBC_ERR_ARG;
+  batch_drop(B, j);
+  return LBC_OK;
+}
+
+lbc_status lbc_batch_remaining(const lbc_batch* B, const lbc_box* b, int64_t* steps) {
+  if (!B || !b || !steps) return LBC_ERR_ARG;
+  const int j = batch_find(B, b);
+  if (j < 0) return LBC_ERR_ARG;
+  *steps = B->members[j].remaining;
+  return LBC_OK;
+}
+
+lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_box** finished,
+                             int32_t* nfinished, int64_t* steps_done) {
+  if (!B || max_steps < 0 || !nfinished || !steps_done) return LBC_ERR_ARG;
+  *nfinished = 0;
+  *steps_done = 0;
+  if (B->members.empty() || max_steps == 0) return LBC_OK;
+  cudaStream_t s = S(stream);
+  int64_t k = max_steps;
+  for (const auto& m : B->members) {
+    if (m.box->status != LBC_OK) return m.box->status;
+    if (m.remaining < k) k = m.remaining;
+  }
+  std::vector<BoxEntry> host;
+  int64_t done = 0;
+  while (done < k) {
+    const int par = B->parity;
+    if (B->steady && k - done >= 2) {
+      if (!B->graph[par] || B->graph_stream[par] != s) {
+        lbc_status st = batch_capture(B, s);
+        if (st != LBC_OK) return st;
+      }
+      CK(cudaGraphLaunch(B->graph[par], s));
+      done += 2;
+    } else {
+      // eager step: the table region is rewritten only after the previous
+      // eager step's launches are done
+      CK(cudaStreamSynchronize(s));
+      BoxEntry* region = B->tables + (size_t)4 * B->max_boxes;
+      int64_t l = 0;
+      lbc_status st = batch_step(B, s, region, host, true, &l);
+      if (st != LBC_OK) return st;
+      B->launches = l;
+      B->steady = true;
+      done += 1;
+    }
+  }
+  for (auto& m : B->members) m.remaining -= k;
+  for (int j = (int)B->members.size() - 1; j >= 0; --j) {
+    if (B->members[j].remaining > 0) continue;
+    if (finished) finished[*nfinished] = B->members[j].box;
+    ++*nfinished;
+    batch_drop(B, j);
+  }
+  *steps_done = k;
+  return last_launch();
+}
+
+int32_t lbc_batch_size(const lbc_batch* B) { return B ? (int32_t)B->members.size() : -1; }
+
+int64_t lbc_batch_launches_per_step(const lbc_batch* B) { return B ? B->launches : -1; }
+
+lbc_status lbc_batch_destroy(lbc_batch* B) {
+  if (!B) return LBC_ERR_ARG;
+  for (auto& m : B->members) m.box->batch = nullptr;
+  B->members.clear();
+  batch_reset_graphs(B);
+  for (int k = 0; k < 2; ++k)
+    if (B->fork[k]) cudaEventDestroy(B->fork[k]);
+  for (cudaStream_t st : B->streams)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : B->events)
+    if (ev) cudaEventDestroy(ev);
+  delete B;
+  return LBC_OK;
+}
 
 }  // extern "C"

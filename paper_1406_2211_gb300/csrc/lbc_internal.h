@@ -34,6 +34,21 @@ struct LBArgs {
 
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,
                     cudaStream_t s);
+
+// One entry of a batched LB launch: a box's arguments, its source and
+// destination population arrays, and its first row in the launch (rows =
+// ny nz per box, in table order; x-rows of at most 128 cells).
+struct BoxEntry {
+  LBArgs a;
+  const void* fin;
+  void* fout;
+  long long row0;
+};
+// 0 BGK, 1 general MRT, 2 MRT with fully relaxed ghosts
+int lb_collision_variant(const LBArgs& a);
+// all boxes of one launch share storage, collision variant, walls and forcing
+void launch_lb_batch(int storage, const BoxEntry* boxes, int nboxes, long long rows, int coll,
+                     bool walls, bool forced, cudaStream_t s);
 // fbar (post-streaming deviations) -> stored pre-streaming form, and back
 void launch_unstream(int storage, const void* fbar, void* fstar, const LBArgs& a,
                      cudaStream_t s);

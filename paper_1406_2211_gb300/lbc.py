@@ -28,6 +28,7 @@ LBC_NONE, LBC_IBM, LBC_FC, LBC_EBF, LBC_MEBF = 0, 1, 2, 3, 4
 LBC_TRILINEAR, LBC_PESKIN4, LBC_PESKIN3 = 0, 1, 2
 LBC_SPLIT_BASE, LBC_SPLIT_INSIDE, LBC_SPLIT_OUTSIDE = 0, 1, 2
 LBC_OPT_GRAPHS = 1
+LBC_BATCH_MAX_NX = 128
 LBC_OPT_TIMING = 2
 LBC_NOALLOC_MAX_PLANES = 4096
 
@@ -90,6 +91,16 @@ _PROTOS = {
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
     "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "lbc_fbar_moments_noalloc": (_S, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
+    "lbc_batch_bytes_required": (C.c_size_t, [C.c_int32]),
+    "lbc_batch_create": (_S, [C.c_int32, _P, C.c_size_t, C.POINTER(_P)]),
+    "lbc_batch_add": (_S, [_P, _P, C.c_int64]),
+    "lbc_batch_remove": (_S, [_P, _P]),
+    "lbc_batch_remaining": (_S, [_P, _P, C.POINTER(C.c_int64)]),
+    "lbc_batch_advance": (_S, [_P, C.c_int64, _P, C.POINTER(_P), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int64)]),
+    "lbc_batch_size": (C.c_int32, [_P]),
+    "lbc_batch_launches_per_step": (C.c_int64, [_P]),
+    "lbc_batch_destroy": (_S, [_P]),
 }
 
 _lib = None
@@ -319,3 +330,78 @@ class Box:
 
     def population_bytes(self):
         return int(self.lib.lbc_box_population_bytes(self.handle))
+
+
+class Batch:
+    """A set of boxes advanced together (lbc_batch_*): continuous batching.
+
+    The box tables live in a torch-allocated device arena.  `add` admits a
+    Box with a step budget, `advance` moves every member forward and returns
+    the Boxes whose budget is spent (they leave the batch)."""
+
+    def __init__(self, max_boxes, stream=None, device="cuda"):
+        import torch
+        lib = library()
+        self.lib = lib
+        self.max_boxes = max_boxes
+        nbytes = int(lib.lbc_batch_bytes_required(max_boxes))
+        if nbytes == 0:
+            raise LBCError(LBC_ERR_ARG, "lbc_batch_bytes_required")
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream
+        h = C.c_void_p()
+        check(lib.lbc_batch_create(max_boxes, C.c_void_p(self.arena.data_ptr()), nbytes,
+                                   C.byref(h)), "lbc_batch_create")
+        self.handle = h
+        self.members = {}          # handle value -> Box
+
+    def _s(self):
+        return _stream_handle(self.stream)
+
+    def add(self, box, steps):
+        """Admit `box` for `steps` steps; returns False if no slot is free."""
+        st = self.lib.lbc_batch_add(self.handle, box.handle, int(steps))
+        if st == LBC_ERR_OOM:
+            return False
+        check(st, "lbc_batch_add")
+        self.members[box.handle.value] = box
+        return True
+
+    def remove(self, box):
+        check(self.lib.lbc_batch_remove(self.handle, box.handle), "lbc_batch_remove")
+        self.members.pop(box.handle.value, None)
+
+    def remaining(self, box):
+        n = C.c_int64()
+        check(self.lib.lbc_batch_remaining(self.handle, box.handle, C.byref(n)),
+              "lbc_batch_remaining")
+        return int(n.value)
+
+    def advance(self, max_steps):
+        """Advance all members by min(max_steps, smallest budget) steps;
+        returns (steps done, list of finished Boxes)."""
+        fin = (C.c_void_p * self.max_boxes)()
+        nfin = C.c_int32()
+        done = C.c_int64()
+        check(self.lib.lbc_batch_advance(self.handle, int(max_steps), self._s(), fin,
+                                         C.byref(nfin), C.byref(done)), "lbc_batch_advance")
+        out = [self.members.pop(fin[k]) for k in range(nfin.value)]
+        return int(done.value), out
+
+    def __len__(self):
+        return int(self.lib.lbc_batch_size(self.handle))
+
+    def launches_per_step(self):
+        return int(self.lib.lbc_batch_launches_per_step(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.lbc_batch_destroy(self.handle)
+            self.handle = None
+            self.members = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

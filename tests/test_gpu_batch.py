@@ -1,0 +1,179 @@
+"""Batched stepping (lbc_batch_*) and the serving loop on the GPU.
+
+A box advanced inside a batch, next to members of other sizes, storage
+formats, coupling kinds and step budgets, must give exactly the results of
+the same box advanced alone (same kernels, same per-box arguments), and the
+same results as stepping the box on its own with lbc_box_step.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_helpers import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _spec(name):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "fc32":
+        return dict(shape=(24, 24, 24), storage="f32", kind="fc", stencil="trilinear", gamma=2.0,
+                    pos=rng.uniform(0, 24, (30, 3)), vel=0.01 * rng.standard_normal((30, 3)))
+    if name == "fc16":
+        return dict(shape=(16, 32, 40), storage="f16dev", kind="fc", stencil="trilinear",
+                    gamma=3.0, pos=rng.uniform(0, 16, (100, 3)) * [2.5, 2.0, 1.0],
+                    vel=0.01 * rng.standard_normal((100, 3)))
+    if name == "fluid":
+        return dict(shape=(20, 20, 20), storage="f32", kind="none", g=(1e-5, 0, 0))
+    if name == "ibm_walls":
+        pos, bonds = synth.bead_chains(2, 6, (16, 16, 12), 1.0, seed=3)
+        pos[:, 2] = 3.0 + np.mod(pos[:, 2], 6.0)
+        return dict(shape=(12, 16, 16), storage="f32", kind="ibm", stencil="peskin4",
+                    walls=True, uw=((-0.02, 0, 0), (0.02, 0, 0)), pos=pos, bonds=bonds)
+    if name == "mrt_bf16":
+        return dict(shape=(18, 20, 22), storage="bf16dev", kind="fc", stencil="peskin4",
+                    coll="mrt", tau=1.0, gamma=1.0, pos=rng.uniform(2, 16, (20, 3)),
+                    vel=0.005 * rng.standard_normal((20, 3)))
+    raise KeyError(name)
+
+
+def _make(spec):
+    from paper_1406_2211_gb300 import lbc
+    nz, ny, nx = spec["shape"]
+    lat = lbc.lattice_desc(nx, ny, nz, collision=spec.get("coll", "bgk"),
+                           tau=spec.get("tau", 0.8), body_force=spec.get("g", (0, 0, 0)),
+                           walls=spec.get("walls", False),
+                           wall_velocity=spec.get("uw", ((0, 0, 0), (0, 0, 0))),
+                           storage=spec["storage"])
+    cpl = lbc.coupling_desc(spec["kind"], 2, spec.get("stencil", "trilinear"),
+                            gamma=spec.get("gamma", 1.0))
+    M = len(spec["pos"]) if "pos" in spec else 0
+    B = len(spec["bonds"]) if "bonds" in spec else 0
+    box = lbc.Box(lat, cpl, max_particles=M, max_bonds=B)
+    fbar = synth.random_populations(spec["shape"], seed=11, amp=1e-3)
+    box.set_populations(fbar)
+    if M:
+        if spec["kind"] == "ibm":
+            box.set_particles(spec["pos"], bonds=spec["bonds"], bond_k=0.05, bond_r0=1.0)
+        else:
+            box.set_particles(spec["pos"], vel=spec["vel"], mass=1.0)
+    return box
+
+
+def _state(box):
+    out = [box.get_populations()]
+    if box.nparticles:
+        out.extend(box.get_particles())
+    return out
+
+
+def _same(a, b):
+    return len(a) == len(b) and all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+NAMES = ["fc32", "fc16", "fluid", "ibm_walls", "mrt_bf16"]
+BUDGET = {"fc32": 9, "fc16": 5, "fluid": 12, "ibm_walls": 9, "mrt_bf16": 7}
+
+
+def _run_batch(names, chunk):
+    from paper_1406_2211_gb300 import lbc
+    import torch
+    batch = lbc.Batch(8)
+    boxes = {n: _make(_spec(n)) for n in names}
+    for n in names:
+        assert batch.add(boxes[n], BUDGET[n])
+    finished = []
+    while len(batch):
+        _, fin = batch.advance(chunk)
+        finished.extend(fin)
+    torch.cuda.synchronize()
+    assert len(finished) == len(names)
+    states = {n: _state(boxes[n]) for n in names}
+    batch.close()
+    return states
+
+
+@pytest.fixture(scope="module")
+def alone():
+    require_cuda()
+    return {n: _run_batch([n], chunk=4)[n] for n in NAMES}
+
+
+def test_member_alone_equals_member_in_mix(alone):
+    mixed = _run_batch(NAMES, chunk=4)
+    for n in NAMES:
+        assert _same(mixed[n], alone[n]), n
+
+
+def test_chunking_does_not_change_results(alone):
+    mixed = _run_batch(NAMES, chunk=3)
+    for n in NAMES:
+        assert _same(mixed[n], alone[n]), n
+
+
+def test_batch_matches_box_stepping(alone):
+    for n in NAMES:
+        box = _make(_spec(n))
+        box.step(BUDGET[n])
+        st = _state(box)
+        ref = alone[n]
+        for x, y in zip(st, ref):
+            assert np.array_equal(x, y), n
+
+
+def test_batch_rules():
+    from paper_1406_2211_gb300 import lbc
+    require_cuda()
+    batch = lbc.Batch(2)
+    a, b, c = (_make(_spec("fluid")) for _ in range(3))
+    assert batch.add(a, 3) and batch.add(b, 3)
+    assert not batch.add(c, 3)                     # no free slot
+    with pytest.raises(lbc.LBCError):              # a member is stepped by its batch
+        a.step(1)
+    assert batch.remaining(a) == 3
+    done, fin = batch.advance(2)
+    assert done == 2 and not fin and batch.remaining(b) == 1
+    batch.remove(b)
+    b.step(1)                                      # free again
+    done, fin = batch.advance(5)
+    assert done == 1 and fin == [a] and len(batch) == 0
+    batch.close()
+
+
+def test_serving_loop_results_equal_alone_runs():
+    require_cuda()
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    from paper_1406_2211_gb300.serve import BoxFactory, Job, JobServer, summary
+    jobs_spec = synth.ensemble_jobs(6, seed=5, edge_range=(16, 40), particles_range=(1, 40),
+                                    steps_range=(5, 25), rate=200.0)
+    jobs = []
+    for i, s in enumerate(jobs_spec):
+        rng = np.random.default_rng(s["seed"])
+        L = s["edge"]
+        spec = dict(edge=L, gamma=s["gamma"], storage=s["storage"],
+                    pos=rng.uniform(0, L, (s["nparticles"], 3)),
+                    vel=0.01 * rng.standard_normal((s["nparticles"], 3)))
+        jobs.append(Job(i, spec, s["arrival"], s["steps"], L ** 3))
+    fac = BoxFactory()
+    batch = lbc.Batch(3)
+    srv = JobServer(fac, batch, memory_budget=2 ** 31, max_active=3, chunk_steps=4,
+                    sync=torch.cuda.synchronize)
+    done = srv.run(jobs)
+    assert len(done) == 6 and srv.peak_active <= 3
+    s = summary(done, srv.elapsed)
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    for j in done:                                  # the same job alone
+        box = fac.create(j)
+        solo = lbc.Batch(1)
+        solo.add(box, j.steps)
+        while len(solo):
+            solo.advance(4)
+        r = fac.result(box)
+        for k in ("pos", "vel", "force_h"):
+            assert np.array_equal(r[k], j.result[k]), (j.id, k)
+        solo.close()
+        fac.release(box)
+    batch.close()
