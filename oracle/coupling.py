@@ -26,8 +26,25 @@ the spreading operator.
 
 Intrinsic forces (the paper's CalculateForces, Alg. 2/3) are model input;
 provided here: harmonic bonds U = k/2 (|d| - r0)^2 between listed pairs
-(minimum-image distance on periodic axes) and a constant external force per
-particle.  Both are pairwise or external, so sum F_int has no internal part.
+(minimum-image distance on periodic axes), a constant external force per
+particle, and rigid bodies made of tethered markers (below).  All are
+pairwise, external, or sum to zero per body, so sum F_int has no internal
+part.
+
+Rigid bodies (a model; the paper has none): body b owns markers
+first_b .. first_b + count_b - 1 with reference sites q_k (body frame,
+centred: sum q_k = 0).  Its frame is the least-squares fit of the markers,
+  X_b = mean of the markers (unwrapped around the first one),
+  R_b = the rotation closest to A = sum_k (y_k - X_b) q_k^T (polar factor,
+        from the SVD A = U S V^T: R = U diag(1, 1, det(U V^T)) V^T),
+and every marker is tethered to its site by a spring,
+  F_k = -k_t (y_k - X_b - R_b q_k).
+X_b and R_b minimise U = k_t/2 sum_k |y_k - X_b - R_b q_k|^2, so F = -grad U
+and the reactions on the (massless) frame vanish: sum_k F_k = 0 and
+sum_k (y_k - X_b) x F_k = 0.  Bodies whose surfaces come closer than one
+lattice unit repel: gap = |X_c - X_b| - (rad_b + rad_c), for gap < 1 a
+force k_rep (1 - gap) along the centre line on each (opposite signs),
+shared equally by the body's markers.
 """
 import numpy as np
 
@@ -59,11 +76,86 @@ def min_image(d, shape, walls):
     return out
 
 
+class RigidBodies:
+    """Bodies of tethered markers: first (B,), count (B,), reference sites
+    ref (M, 3) relative to the body centre (centred per body), tether
+    stiffness k_t, repulsion stiffness k_rep, radius (B,)."""
+
+    def __init__(self, first, count, ref, k_t, k_rep, radius):
+        self.first = np.array(first, dtype=np.int64).reshape(-1)
+        self.count = np.array(count, dtype=np.int64).reshape(-1)
+        self.ref = np.array(ref, dtype=np.float64).reshape(-1, 3)
+        self.k_t = float(k_t)
+        self.k_rep = float(k_rep)
+        self.radius = np.broadcast_to(np.asarray(radius, dtype=np.float64),
+                                      self.first.shape).copy()
+
+    @staticmethod
+    def from_positions(pos, first, count, k_t, k_rep, radius, shape, walls):
+        """Reference sites from a configuration taken as the rest shape."""
+        ref = np.zeros((pos.shape[0], 3))
+        for f, c in zip(first, count):
+            y = _unwrapped(pos[f:f + c], shape, walls)
+            ref[f:f + c] = y - y.mean(axis=0)
+        return RigidBodies(first, count, ref, k_t, k_rep, radius)
+
+    def copy(self):
+        return RigidBodies(self.first, self.count, self.ref, self.k_t, self.k_rep,
+                           self.radius)
+
+
+def _unwrapped(x, shape, walls):
+    """Marker positions of one body as a connected set: the first one as
+    is, the others at their minimum image relative to it."""
+    return x[0] + min_image(x - x[0], shape, walls)
+
+
+def rigid_frames(bodies, pos, shape, walls):
+    """Centre X (B, 3) and rotation R (B, 3, 3) of every body, and the
+    unwrapped marker positions y (M, 3)."""
+    B = bodies.first.shape[0]
+    X = np.zeros((B, 3))
+    R = np.zeros((B, 3, 3))
+    y = pos.copy()
+    for b in range(B):
+        f, c = bodies.first[b], bodies.count[b]
+        yb = _unwrapped(pos[f:f + c], shape, walls)
+        y[f:f + c] = yb
+        X[b] = yb.mean(axis=0)
+        A = (yb - X[b]).T @ bodies.ref[f:f + c]
+        U, _, Vt = np.linalg.svd(A)
+        d = np.sign(np.linalg.det(U @ Vt))
+        R[b] = U @ np.diag([1.0, 1.0, d]) @ Vt
+    return X, R, y
+
+
+def rigid_forces(bodies, pos, shape, walls):
+    """Tether forces of every marker plus the pairwise body repulsion."""
+    F = np.zeros_like(pos)
+    X, R, y = rigid_frames(bodies, pos, shape, walls)
+    B = X.shape[0]
+    for b in range(B):
+        f, c = bodies.first[b], bodies.count[b]
+        sites = X[b] + bodies.ref[f:f + c] @ R[b].T
+        F[f:f + c] = -bodies.k_t * (y[f:f + c] - sites)
+    for b in range(B):
+        for c2 in range(b + 1, B):
+            d = min_image((X[c2] - X[b])[None, :], shape, walls)[0]
+            dist = np.sqrt(d @ d)
+            gap = dist - (bodies.radius[b] + bodies.radius[c2])
+            if gap < 1.0:
+                fc = bodies.k_rep * (1.0 - gap) * d / dist        # on body c2
+                F[bodies.first[c2]:bodies.first[c2] + bodies.count[c2]] += fc / bodies.count[c2]
+                F[bodies.first[b]:bodies.first[b] + bodies.count[b]] -= fc / bodies.count[b]
+    return F
+
+
 class Particles:
-    """Lagrangian points: positions, velocities, masses, bonds, external force."""
+    """Lagrangian points: positions, velocities, masses, bonds, external
+    force, rigid bodies."""
 
     def __init__(self, pos, vel=None, mass=None, bonds=None, bond_k=None,
-                 bond_r0=None, ext_force=None):
+                 bond_r0=None, ext_force=None, rigid=None):
         self.pos = np.array(pos, dtype=np.float64).reshape(-1, 3)
         M = self.pos.shape[0]
         self.vel = np.zeros((M, 3)) if vel is None else \
@@ -79,15 +171,19 @@ class Particles:
             np.broadcast_to(np.asarray(bond_r0, dtype=np.float64), (nb,)).copy()
         self.ext_force = np.zeros((M, 3)) if ext_force is None else \
             np.array(ext_force, dtype=np.float64).reshape(M, 3)
+        self.rigid = rigid
 
     def copy(self):
         return Particles(self.pos, self.vel, self.mass, self.bonds, self.bond_k,
-                         self.bond_r0, self.ext_force)
+                         self.bond_r0, self.ext_force,
+                         None if self.rigid is None else self.rigid.copy())
 
 
 def intrinsic_forces(parts, pos, shape, walls):
-    """F_int(X): harmonic bonds plus constant external forces."""
+    """F_int(X): harmonic bonds, constant external forces, rigid bodies."""
     F = parts.ext_force.copy()
+    if parts.rigid is not None:
+        F += rigid_forces(parts.rigid, pos, shape, walls)
     if parts.bonds.shape[0]:
         i, j = parts.bonds[:, 0], parts.bonds[:, 1]
         d = min_image(pos[j] - pos[i], shape, walls)

@@ -15,7 +15,7 @@ import numpy as np
 __all__ = [
     "D3Q19_WEIGHTS", "random_populations", "shear_wave", "rest_fields",
     "random_points", "bead_chains", "icosphere", "place_spheres",
-    "fibonacci_sphere", "shells", "ensemble_jobs", "CONFIGS", "config",
+    "fibonacci_sphere", "shells", "rigid_spheres", "ensemble_jobs", "CONFIGS", "config",
 ]
 
 # lattice weights in the D3Q19 ordering used by both implementations: rest,
@@ -169,6 +169,21 @@ def shells(nshells, radius, box, seed, subdivisions=3, wall_clearance=3.0):
     return pos, edges.astype(np.int32), r0
 
 
+def rigid_spheres(nspheres, radius, markers, box, seed, gap=1.0):
+    """Surface markers of non-overlapping spheres: Fibonacci points on each
+    sphere of the given radius.  Returns (pos (n*markers, 3) wrapped into the
+    periodic box, first (n,), count (n,))."""
+    centres = place_spheres(nspheres, radius, box, seed, gap=gap)
+    v = fibonacci_sphere(markers)
+    box = np.asarray(box, dtype=np.float64)
+    pos = (centres[:, None, :] + radius * v[None, :, :]).reshape(-1, 3)
+    pos = np.mod(pos, box)
+    pos = np.where(pos >= box, pos - box, pos)
+    first = np.arange(nspheres) * markers
+    count = np.full(nspheres, markers)
+    return pos, first.astype(np.int32), count.astype(np.int32)
+
+
 def ensemble_jobs(njobs, seed, edge_range=(32, 128), particles_range=(1, 5000),
                   gamma_range=(0.5, 10.0), steps_range=(1000, 20000),
                   rate=None):
@@ -219,7 +234,11 @@ CONFIGS = {
     "cfg4_mebf_spheres_128": dict(
         box=(128, 128, 128), collision="bgk", tau=0.7, storage="f32",
         rho0=1.0, kind="mebf", stencil="peskin4", nspheres=500, radius=4.5,
-        markers=400, seed=12345, steps=5000),
+        markers=400, seed=12345, steps=5000,
+        # rigid-sphere model (not in the paper): markers of mass
+        # rho0 (4/3) pi R^3 / markers tethered to the best-fit rigid frame
+        # (stiffness rigid_k), soft repulsion below a one-unit gap
+        rigid_k=1.0, repulsion_k=0.1),
     "cfg5_ensemble": dict(njobs=2000, seed=12345, collision="bgk", tau=0.8,
                           kind="fc", mass=1.0, stencil="trilinear"),
 }
