@@ -118,6 +118,25 @@ typedef struct lbc_particles_desc {
   const int32_t* bond_ij;    /* [nbonds][2] particle indices */
   const double* bond_k;      /* [nbonds] spring constants */
   const double* bond_r0;     /* [nbonds] rest lengths */
+  /* Rigid bodies of tethered markers (a model; the paper has none).  Body b
+   * owns markers rigid_first[b] .. rigid_first[b] + rigid_count[b] - 1
+   * (disjoint ranges).  Its frame is the least-squares fit of the markers:
+   * centre X_b = their mean (unwrapped around the first marker) and
+   * rotation R_b = the polar factor of A = sum_k (y_k - X_b) q_k^T, where
+   * q_k are the marker's reference sites (body frame, centred).  Each
+   * marker feels F = -rigid_k (y_k - X_b - R_b q_k); bodies whose surfaces
+   * (radius rigid_radius[b]) come closer than one lattice unit repel with
+   * rigid_repulsion_k (1 - gap) along the centre line, shared equally by
+   * the body's markers.  Frames are evaluated wherever F_int is. */
+  int64_t nrigid;            /* number of bodies (0: none) */
+  const int32_t* rigid_first;   /* [nrigid] */
+  const int32_t* rigid_count;   /* [nrigid] */
+  const double* rigid_radius;   /* [nrigid] */
+  const double* rigid_ref;      /* [n][3] reference sites q_k relative to the
+                                   body centre (NULL: taken from pos as the
+                                   rest shape); used for markers in bodies */
+  double rigid_k;               /* tether stiffness */
+  double rigid_repulsion_k;     /* repulsion stiffness */
 } lbc_particles_desc;
 
 typedef struct lbc_box lbc_box;

@@ -18,7 +18,7 @@ using namespace lbc;
 
 namespace {
 
-constexpr int32_t ABI_VERSION = 1;
+constexpr int32_t ABI_VERSION = 2;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -64,6 +64,9 @@ struct Layout {
   size_t off_nbr_start, off_nbr_j, off_nbr_kr, off_nbr_r0sq;
   size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
   size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
+  // rigid bodies (at most one per marker)
+  size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
+      off_rb_frep;
   size_t off_red, off_redout;
   int ntiles, maxnt;
   bool has_particles;
@@ -129,6 +132,13 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_ncache = take(multistep ? (size_t)sn * sn * sn * 4 * M * force_elem_bytes(l->storage) : 0);
     L.off_ncache_b = take(multistep ? (size_t)M * 16 : 0);
     L.use_ncache = multistep;
+    L.off_rb_first = take((size_t)M * 4);
+    L.off_rb_count = take((size_t)M * 4);
+    L.off_rb_radius = take((size_t)M * 8);
+    L.off_rb_body_of = take((size_t)M * 4);
+    L.off_rb_ref = take(v3);
+    L.off_rb_frames = take((size_t)M * 12 * 8);
+    L.off_rb_frep = take(v3);
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
@@ -167,6 +177,8 @@ struct lbc_box {
   LBArgs lb;        // constant part of the LB arguments
   int64_t launches;
   BoxEntry deferred;   // the LB step recorded by a phase-1 pass (batched launch)
+  int64_t nrigid;      // rigid bodies set by lbc_box_set_particles
+  double rigid_k, rigid_krep;
   lbc_batch* batch;    // the batch this box belongs to, or null
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
@@ -312,6 +324,22 @@ struct Plan {
     d.nbr_j = b->iptr(b->L.off_nbr_j);
     d.nbr_kr = b->arena + b->L.off_nbr_kr;
     d.nbr_r0sq = b->dptr(b->L.off_nbr_r0sq);
+    if (force && b->nrigid > 0) {
+      RigidArgs& r = d.rigid;
+      r.nbodies = (int)b->nrigid;
+      r.first = b->iptr(b->L.off_rb_first);
+      r.count = b->iptr(b->L.off_rb_count);
+      r.radius = b->dptr(b->L.off_rb_radius);
+      r.body_of = b->iptr(b->L.off_rb_body_of);
+      r.ref = b->dptr(b->L.off_rb_ref);
+      r.k = b->rigid_k;
+      r.krep = b->rigid_krep;
+      r.frames = b->dptr(b->L.off_rb_frames);
+      r.frep = b->dptr(b->L.off_rb_frep);
+      r.status = b->iptr(b->L.off_status);
+      launch_rigid_frames(part_args(b), d, s);
+      n += 2;
+    }
     launch_drift(part_args(b), d, s);
     if (write) b->pc = 1 - b->pc;
     if (key) b->sorted = false;
@@ -799,6 +827,8 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->status = LBC_OK;
   b->launches = 0;
   b->batch = nullptr;
+  b->nrigid = 0;
+  b->rigid_k = b->rigid_krep = 0.0;
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -957,6 +987,43 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
       if (!(p->mass[i] > 0.0)) return LBC_ERR_ARG;
       mass[i] = p->mass[i];
     }
+  // rigid bodies: marker ranges, body of each marker, reference sites
+  const int64_t B = p->nrigid;
+  if (B < 0 || B > M) return LBC_ERR_ARG;
+  std::vector<int> rfirst(B > 0 ? B : 1, 0), rcount(B > 0 ? B : 1, 0), body_of(M > 0 ? M : 1, -1);
+  std::vector<double> rradius(B > 0 ? B : 1, 0.0), rref(3 * (M > 0 ? M : 1), 0.0);
+  if (B > 0) {
+    if (!p->rigid_first || !p->rigid_count || !p->rigid_radius || !(p->rigid_k >= 0.0) ||
+        !(p->rigid_repulsion_k >= 0.0))
+      return LBC_ERR_ARG;
+    for (int64_t r = 0; r < B; ++r) {
+      const int f = p->rigid_first[r], c = p->rigid_count[r];
+      if (f < 0 || c < 1 || (int64_t)f + c > M || !(p->rigid_radius[r] >= 0.0)) return LBC_ERR_ARG;
+      for (int k = f; k < f + c; ++k) {
+        if (body_of[k] >= 0) return LBC_ERR_ARG;          // ranges must be disjoint
+        body_of[k] = (int)r;
+      }
+      rfirst[r] = f; rcount[r] = c; rradius[r] = p->rigid_radius[r];
+      if (p->rigid_ref) {
+        for (int k = f; k < f + c; ++k)
+          for (int a = 0; a < 3; ++a) rref[a * M + k] = p->rigid_ref[3 * k + a];
+      } else {
+        // rest shape = the given configuration: unwrap around the first
+        // marker (minimum image on periodic axes) and centre
+        double mean[3] = {0.0, 0.0, 0.0};
+        for (int k = f; k < f + c; ++k)
+          for (int a = 0; a < 3; ++a) {
+            double dd = pos[a * M + k] - pos[a * M + f];
+            if (a < 2 || !g.walls) dd -= n3[a] * std::nearbyint(dd / n3[a]);
+            rref[a * M + k] = pos[a * M + f] + dd;
+            mean[a] += rref[a * M + k];
+          }
+        for (int a = 0; a < 3; ++a) mean[a] /= c;
+        for (int k = f; k < f + c; ++k)
+          for (int a = 0; a < 3; ++a) rref[a * M + k] -= mean[a];
+      }
+    }
+  }
   // bonds as a per-particle adjacency list (CSR), in bond order
   std::vector<int> start(M + 1, 0), nj(2 * p->nbonds > 0 ? 2 * p->nbonds : 1, 0);
   std::vector<double> nk(nj.size(), 0.0), nr(nj.size(), 0.0);
@@ -1010,6 +1077,16 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   CK(cudaMemcpyAsync(b->iptr(b->L.off_nbr_j), nj.data(), nj.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->arena + b->L.off_nbr_kr, kr_c.data(), kr_c.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->dptr(b->L.off_nbr_r0sq), r0sq.data(), r0sq.size() * 8, cudaMemcpyHostToDevice, s));
+  if (B > 0) {
+    CK(cudaMemcpyAsync(b->iptr(b->L.off_rb_first), rfirst.data(), B * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->iptr(b->L.off_rb_count), rcount.data(), B * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->dptr(b->L.off_rb_radius), rradius.data(), B * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->iptr(b->L.off_rb_body_of), body_of.data(), M * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->dptr(b->L.off_rb_ref), rref.data(), 3 * M * 8, cudaMemcpyHostToDevice, s));
+  }
+  b->nrigid = B;
+  b->rigid_k = B > 0 ? p->rigid_k : 0.0;
+  b->rigid_krep = B > 0 ? p->rigid_repulsion_k : 0.0;
   b->sorted = false;
   reset_graphs(b);
   CK(cudaStreamSynchronize(s));

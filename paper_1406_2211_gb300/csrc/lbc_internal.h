@@ -96,6 +96,21 @@ struct PartArgs {
   int storage;          // selects the compute type of fields and records
 };
 
+// Rigid bodies of tethered markers (see particle_kernels.cu): per body the
+// best-fit frame of its markers at the pre-drifted positions, then the
+// tether force of every marker and a soft body-body repulsion.
+struct RigidArgs {
+  int nbodies;
+  const int* first; const int* count;     // marker range of each body
+  const double* radius;                   // [B]
+  const int* body_of;                     // [M] body of each marker, -1: none
+  const double* ref;                      // [3][M] reference sites (body frame)
+  double k, krep;                         // tether and repulsion stiffness
+  double* frames;                         // [B][12]: X (3), R (9, row-major)
+  double* frep;                           // [B][3] repulsion force on the body
+  int* status;                            // set to 2 if a frame is degenerate
+};
+
 // drift / intrinsic force / kick / drift sub-step (see particle_kernels.cu):
 //   r <- wrap(wrap(r + dt_pre0 v) + dt_pre v); F = F_int(r);
 //   v <- v + dt_kick F / m; r <- wrap(r + dt_post v)
@@ -111,8 +126,12 @@ struct DriftArgs {
   const int* nbr_start; const int* nbr_j;       // bonds per particle (CSR)
   const void* nbr_kr;                            // (k, r0) per entry, compute type
   const double* nbr_r0sq;                        // r0^2 per entry
+  RigidArgs rigid;                               // nbodies == 0: no rigid bodies
 };
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
+// frames and repulsion of the rigid bodies at the pre-drifted positions of
+// a drift with compute_force (launched before it)
+void launch_rigid_frames(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
 
 // LSD radix sort of (key, idx) pairs; ping-pong buffers, result in *_a
 size_t sort_scratch_ints(long long M);

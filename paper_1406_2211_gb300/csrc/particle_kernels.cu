@@ -165,6 +165,21 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
       const C mag = k * stretch / dist;
       for (int c = 0; c < 3; ++c) F[c] += ec[c] * mag;
     }
+    const int body = d.rigid.nbodies > 0 ? d.rigid.body_of[i] : -1;
+    if (body >= 0) {
+      // tether to the body's best-fit frame: F = -k (y - X - R q), the
+      // difference taken at its minimum image; plus the body's share of
+      // the repulsion
+      const double* fr = d.rigid.frames + 12 * body;
+      const double q[3] = {d.rigid.ref[i], d.rigid.ref[M + i], d.rigid.ref[2 * M + i]};
+      const double inv_n = 1.0 / (double)d.rigid.count[body];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double site = fr[c] + fr[3 + 3 * c] * q[0] + fr[4 + 3 * c] * q[1] + fr[5 + 3 * c] * q[2];
+        const double dev = min_image(r1[c] - site, n3[c], per[c]);
+        F[c] += (C)(-d.rigid.k * dev + d.rigid.frep[3 * body + c] * inv_n);
+      }
+    }
     if (d.fint_out) {
       C* fo = static_cast<C*>(d.fint_out);
       for (int c = 0; c < 3; ++c) fo[c * M + i] = F[c];
@@ -185,6 +200,149 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
     d.key_out[i] = key_of(g, r2[0], r2[1], r2[2]);
     d.idx_out[i] = (uint32_t)i;
   }
+}
+
+// ------------------------------------------------------------ rigid bodies
+constexpr int FRAME_THREADS = 128;
+
+// 3x3 helpers (row-major)
+__device__ inline double det3(const double* a) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+         a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+// inverse transpose = cofactor matrix / det
+__device__ inline void inv_transpose3(const double* a, double det, double* out) {
+  const double r = 1.0 / det;
+  out[0] = (a[4] * a[8] - a[5] * a[7]) * r;
+  out[1] = (a[5] * a[6] - a[3] * a[8]) * r;
+  out[2] = (a[3] * a[7] - a[4] * a[6]) * r;
+  out[3] = (a[2] * a[7] - a[1] * a[8]) * r;
+  out[4] = (a[0] * a[8] - a[2] * a[6]) * r;
+  out[5] = (a[1] * a[6] - a[0] * a[7]) * r;
+  out[6] = (a[1] * a[5] - a[2] * a[4]) * r;
+  out[7] = (a[2] * a[3] - a[0] * a[5]) * r;
+  out[8] = (a[0] * a[4] - a[1] * a[3]) * r;
+}
+
+// block-wide sum of n values per thread (shared scratch sh[n][FRAME_THREADS])
+template <int NV>
+__device__ inline void block_sum(double (&v)[NV], double (*sh)[FRAME_THREADS]) {
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = FRAME_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  for (int k = 0; k < NV; ++k) v[k] = sh[k][0];
+  __syncthreads();
+}
+
+// One block per body: the markers at their pre-drifted positions r1 (the
+// drift's own formula), unwrapped around the first marker; X = their mean,
+// R = polar factor of A = sum (y - X) q^T by the scaled Newton iteration
+// R <- (g R + (g R)^-T) / 2, g = |det R|^(-1/3) (converges to the
+// orthogonal factor, a proper rotation while det A > 0).
+__global__ void __launch_bounds__(FRAME_THREADS)
+rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
+  __shared__ double sh[9][FRAME_THREADS];
+  const RigidArgs& rg = d.rigid;
+  const int b = blockIdx.x;
+  const long long M = p.M;
+  const Geom& g = p.g;
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const bool per[3] = {true, true, !g.walls};
+  const int f = rg.first[b], cnt = rg.count[b];
+  double r0[3];
+  for (int c = 0; c < 3; ++c) {
+    const double v = d.vel_in[c * M + f];
+    r0[c] = (d.pos_in[c * M + f] + d.dt_pre0 * v) + d.dt_pre * v;
+  }
+  auto y_of = [&](long long i, double (&y)[3]) {
+    for (int c = 0; c < 3; ++c) {
+      const double v = d.vel_in[c * M + i];
+      const double r1 = (d.pos_in[c * M + i] + d.dt_pre0 * v) + d.dt_pre * v;
+      y[c] = r0[c] + min_image(r1 - r0[c], n3[c], per[c]);
+    }
+  };
+  double s3[3] = {0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
+    double y[3];
+    y_of(f + k, y);
+    for (int c = 0; c < 3; ++c) s3[c] += y[c];
+  }
+  block_sum<3>(s3, sh);
+  const double X[3] = {s3[0] / cnt, s3[1] / cnt, s3[2] / cnt};
+  double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
+    const long long i = f + k;
+    double y[3];
+    y_of(i, y);
+    const double q[3] = {rg.ref[i], rg.ref[M + i], rg.ref[2 * M + i]};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) A[3 * r + c] += (y[r] - X[r]) * q[c];
+  }
+  block_sum<9>(A, sh);
+  if (threadIdx.x == 0) {
+    double R[9], Ri[9];
+    for (int k = 0; k < 9; ++k) R[k] = A[k];
+    double det = det3(R);
+    bool ok = det > 0.0;
+    for (int it = 0; ok && it < 40; ++it) {
+      const double gsc = 1.0 / cbrt(det);
+      for (int k = 0; k < 9; ++k) R[k] *= gsc;
+      inv_transpose3(R, 1.0, Ri);          // det of the scaled matrix is 1
+      double diff = 0.0;
+      for (int k = 0; k < 9; ++k) {
+        const double nr = 0.5 * (R[k] + Ri[k]);
+        diff = fmax(diff, fabs(nr - R[k]));
+        R[k] = nr;
+      }
+      det = det3(R);
+      if (diff < 1e-15) break;
+    }
+    if (!ok) {
+      *rg.status = 2;
+      for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    }
+    double* out = rg.frames + 12 * b;
+    for (int c = 0; c < 3; ++c) out[c] = X[c];
+    for (int k = 0; k < 9; ++k) out[3 + k] = R[k];
+  }
+}
+
+// one thread per body: repulsion from every other body closer than one
+// lattice unit (surface gap), summed in body order
+__global__ void rigid_repulsion_kernel(const PartArgs p, const RigidArgs rg) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= rg.nbodies) return;
+  const Geom& g = p.g;
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const bool per[3] = {true, true, !g.walls};
+  const double* Xb = rg.frames + 12 * b;
+  double Fb[3] = {0.0, 0.0, 0.0};
+  for (int c2 = 0; c2 < rg.nbodies; ++c2) {
+    if (c2 == b) continue;
+    const double* Xc = rg.frames + 12 * c2;
+    double dv[3], d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      dv[c] = min_image(Xc[c] - Xb[c], n3[c], per[c]);
+      d2 += dv[c] * dv[c];
+    }
+    const double dist = sqrt(d2);
+    const double gap = dist - (rg.radius[b] + rg.radius[c2]);
+    if (gap < 1.0 && dist > 0.0) {
+      const double mag = rg.krep * (1.0 - gap) / dist;      // pushes b away from c2
+      for (int c = 0; c < 3; ++c) Fb[c] -= mag * dv[c];
+    }
+  }
+  for (int c = 0; c < 3; ++c) rg.frep[3 * b + c] = Fb[c];
+}
+
+void launch_rigid_frames(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
+  if (d.rigid.nbodies <= 0) return;
+  rigid_frames_kernel<<<d.rigid.nbodies, FRAME_THREADS, 0, s>>>(p, d);
+  rigid_repulsion_kernel<<<(d.rigid.nbodies + 127) / 128, 128, 0, s>>>(p, d.rigid);
 }
 
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {

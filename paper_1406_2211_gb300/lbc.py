@@ -61,7 +61,11 @@ class lbc_particles_desc(C.Structure):
     _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("vel", C.c_void_p),
                 ("mass", C.c_void_p), ("ext_force", C.c_void_p),
                 ("nbonds", C.c_int64), ("bond_ij", C.c_void_p),
-                ("bond_k", C.c_void_p), ("bond_r0", C.c_void_p)]
+                ("bond_k", C.c_void_p), ("bond_r0", C.c_void_p),
+                ("nrigid", C.c_int64), ("rigid_first", C.c_void_p),
+                ("rigid_count", C.c_void_p), ("rigid_radius", C.c_void_p),
+                ("rigid_ref", C.c_void_p), ("rigid_k", C.c_double),
+                ("rigid_repulsion_k", C.c_double)]
 
 
 _P = C.c_void_p
@@ -259,7 +263,8 @@ class Box:
               "lbc_box_set_pending_force")
 
     def set_particles(self, pos, vel=None, mass=None, ext_force=None, bonds=None,
-                      bond_k=None, bond_r0=None):
+                      bond_k=None, bond_r0=None, rigid=None):
+        """rigid: dict(first, count, radius, k, repulsion_k[, ref]) or None."""
         pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         n = pos.shape[0]
         arrs = dict(pos=pos)
@@ -284,6 +289,19 @@ class Box:
             arrs.update(bij=bij, bk=bk, br=br)
             d.nbonds = nb
             d.bond_ij, d.bond_k, d.bond_r0 = _ptr(bij), _ptr(bk), _ptr(br)
+        if rigid is not None:
+            rf = np.ascontiguousarray(rigid["first"], dtype=np.int32).reshape(-1)
+            rc = np.ascontiguousarray(rigid["count"], dtype=np.int32).reshape(-1)
+            rr = np.ascontiguousarray(np.broadcast_to(np.asarray(rigid["radius"], dtype=np.float64),
+                                                      rf.shape))
+            arrs.update(rf=rf, rc=rc, rr=rr)
+            d.nrigid = rf.shape[0]
+            d.rigid_first, d.rigid_count, d.rigid_radius = _ptr(rf), _ptr(rc), _ptr(rr)
+            if rigid.get("ref") is not None:
+                arrs["rq"] = np.ascontiguousarray(rigid["ref"], dtype=np.float64).reshape(n, 3)
+                d.rigid_ref = _ptr(arrs["rq"])
+            d.rigid_k = float(rigid["k"])
+            d.rigid_repulsion_k = float(rigid.get("repulsion_k", 0.0))
         check(self.lib.lbc_box_set_particles(self.handle, C.byref(d), self._s()),
               "lbc_box_set_particles")
         self.nparticles = n

@@ -38,16 +38,21 @@ def make_pair(shape, fbar0, coll="bgk", tau=0.8, lam=(0, 0, 0, 0), g=(0, 0, 0),
                     walls=walls, u_bot=uw[0], u_top=uw[1])
     oparts = None
     if parts is not None:
+        rig = parts.get("rigid")
         box.set_particles(parts["pos"], vel=parts.get("vel"), mass=parts.get("mass"),
                           ext_force=parts.get("ext"), bonds=parts.get("bonds"),
-                          bond_k=parts.get("bond_k"), bond_r0=parts.get("bond_r0"))
+                          bond_k=parts.get("bond_k"), bond_r0=parts.get("bond_r0"), rigid=rig)
         M = len(parts["pos"])
         mass = parts.get("mass")
+        orig = None if rig is None else OC.RigidBodies(rig["first"], rig["count"], rig["ref"],
+                                                        rig["k"], rig.get("repulsion_k", 0.0),
+                                                        rig["radius"])
         oparts = OC.Particles(OC.wrap_positions(np.asarray(parts["pos"], float), shape, walls),
                               vel=parts.get("vel"),
                               mass=None if mass is None else np.broadcast_to(mass, (M,)),
                               bonds=parts.get("bonds"), bond_k=parts.get("bond_k"),
-                              bond_r0=parts.get("bond_r0"), ext_force=parts.get("ext"))
+                              bond_r0=parts.get("bond_r0"), ext_force=parts.get("ext"),
+                              rigid=orig)
     mode = {"base": "base", "inside": "inside", "outside": "outside"}[split]
     sm = OS.Sim(shape, p, OS.CouplingParams(kind, order, stencil, gamma=gamma,
                                             substeps=n, mode=mode),

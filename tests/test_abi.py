@@ -54,7 +54,7 @@ def test_descriptor_sizes_match(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.lbc_abi_version() == 1
+    assert lib.lbc_abi_version() == 2
     assert lib.lbc_status_string(0) == b"ok"
     assert lib.lbc_status_string(-2) == b"caller memory too small"
     assert lib.lbc_status_string(99) == b"unknown status"
