@@ -222,6 +222,30 @@ def physical_velocity(fbar, Fa, p, order=2):
     return j / rho
 
 
+def viscous_stress(fbar, p):
+    """Viscous stress of the post-streaming populations, Eq. [viscstress]
+    (first line, Sec. 3.4):
+
+        sigma = 1/2 (1 + (1 - Lambda_1/2)^2) sum_i (fbar_i - f^eq_i) c_i c_i
+
+    with (1 - Lambda_1/2)^2 = 1 - Lambda the full-step collision eigenvalues
+    (gamma for BGK, diag(gamma_k) in the moment basis for MRT) and f^eq at
+    the density and velocity of fbar (a force half step leaves fbar - f^eq
+    unchanged).  Returns sigma[a, b, z, y, x].
+    """
+    rho = L.density(fbar)
+    feq = L.equilibrium(rho, L.momentum(fbar) / rho)
+    fneq = fbar - feq
+    gam = p.gamma_full()
+    if p.collision == 'bgk':
+        scaled = 0.5 * (1.0 + gam) * fneq
+    else:
+        m = np.tensordot(L.MRT_E, fneq, axes=([1], [0]))
+        m = 0.5 * (1.0 + np.asarray(gam)).reshape((L.Q,) + (1,) * (fbar.ndim - 1)) * m
+        scaled = np.tensordot(np.linalg.inv(L.MRT_E), m, axes=([1], [0]))
+    return np.einsum('ia,ib,i...->ab...', L.CF, L.CF, scaled)
+
+
 def half_collision_approx(f, p):
     """The O(h^2) half collision (1 + C)/2 of Eq. [half-col-approx].
 
