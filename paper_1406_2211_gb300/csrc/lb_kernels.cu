@@ -485,6 +485,67 @@ __global__ void fields_kernel(const S* __restrict__ fstar, const LBArgs a, doubl
   rho_out[dense] = rho;
 }
 
+// Viscous stress of the post-streaming populations, Eq. [viscstress] (first
+// line): sigma = 1/2 (1 + (1 - Lambda_1/2)^2) sum_i (fbar_i - f^eq_i) c_i c_i.
+// The non-equilibrium second moment (FP64 sums of the pulled deviations)
+// Pi^neq = sum dev c c - (rd / 3) I - j j / rho splits into its trace part
+// (bulk moment, eigenvalue gamma_b) and its traceless part (shear moments,
+// gamma_s); the other moments carry no second moment.  BGK: gamma_b =
+// gamma_s.  Components xx, yy, zz, xy, yz, xz; `half` selects 0-2 or 3-5
+// (the staging buffer holds three at a time).
+template <typename S>
+__global__ void stress_kernel(const S* __restrict__ fstar, const LBArgs a, int half,
+                              double* __restrict__ out) {
+  using C = typename Store<S>::C;
+  const Geom& g = a.g;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long dense = ((long long)z * g.ny + y) * g.nx + x;
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  C f[Q];
+  if (g.walls) pull_cell<S, true>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  else pull_cell<S, false>(fstar, g, a.bb_bot, a.bb_top, a.scale16, x, y, z, f);
+  double rd = 0, j[3] = {0, 0, 0}, P[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double v = double(f[i]);
+    const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+    rd += v;
+    for (int k = 0; k < 3; ++k) j[k] += c[k] * v;
+    P[0] += c[0] * c[0] * v; P[1] += c[1] * c[1] * v; P[2] += c[2] * c[2] * v;
+    P[3] += c[0] * c[1] * v; P[4] += c[1] * c[2] * v; P[5] += c[0] * c[2] * v;
+  }
+  const double rho = a.rho0.d + rd;
+  const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {1, 2}, {0, 2}};
+  double nq[6];
+  for (int k = 0; k < 6; ++k) {
+    nq[k] = P[k] - j[ab[k][0]] * j[ab[k][1]] / rho;
+    if (k < 3) nq[k] -= rd / 3.0;
+  }
+  const double gb = a.collision == 0 ? a.gamma_bgk.d : a.gamma_k[0].d;
+  const double gs = a.collision == 0 ? a.gamma_bgk.d : a.gamma_k[1].d;
+  const double tr3 = (nq[0] + nq[1] + nq[2]) / 3.0;
+  double sg[6];
+  for (int k = 0; k < 6; ++k) {
+    const double iso = k < 3 ? tr3 : 0.0;
+    sg[k] = 0.5 * (1.0 + gb) * iso + 0.5 * (1.0 + gs) * (nq[k] - iso);
+  }
+  for (int k = 0; k < 3; ++k) out[k * N + dense] = sg[3 * half + k];
+}
+
+void launch_stress(int storage, const void* fstar, const LBArgs& a, int half, double* out,
+                   cudaStream_t s) {
+  int bx;
+  dim3 grid = cell_grid(a.g, &bx);
+  switch (storage) {
+    case ST_F64: stress_kernel<double><<<grid, bx, 0, s>>>(static_cast<const double*>(fstar), a, half, out); break;
+    case ST_F32: stress_kernel<float><<<grid, bx, 0, s>>>(static_cast<const float*>(fstar), a, half, out); break;
+    case ST_F16: stress_kernel<__half><<<grid, bx, 0, s>>>(static_cast<const __half*>(fstar), a, half, out); break;
+    default: stress_kernel<__nv_bfloat16><<<grid, bx, 0, s>>>(static_cast<const __nv_bfloat16*>(fstar), a, half, out); break;
+  }
+}
+
 constexpr int RED_THREADS = 256;
 
 int invariants_blocks(const Geom& g) {

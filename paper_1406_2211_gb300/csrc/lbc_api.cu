@@ -1118,6 +1118,21 @@ lbc_status lbc_box_get_fields(lbc_box* b, double* rho, double* u, void* stream) 
   return last_launch();
 }
 
+lbc_status lbc_box_get_stress(lbc_box* b, double* sigma, void* stream) {
+  if (!b || !sigma) return LBC_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const Geom& g = b->L.g;
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  if (3 * N * sizeof(double) > b->L.pop_bytes) return LBC_ERR_UNSUPPORTED;
+  double* stage = static_cast<double*>(b->pop(1 - b->cur));
+  for (int half = 0; half < 2; ++half) {
+    launch_stress(b->lat.storage, b->pop(b->cur), b->lb, half, stage, s);
+    CK(cudaMemcpyAsync(sigma + 3 * half * N, stage, 3 * N * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return last_launch();
+}
+
 lbc_status lbc_box_get_particles(lbc_box* b, double* pos, double* vel, double* fh, void* stream) {
   if (!b) return LBC_ERR_ARG;
   if (b->M == 0) return LBC_OK;

@@ -63,6 +63,10 @@ void launch_fields(int storage, const void* fstar, const LBArgs& a,
 void launch_init_eq(int storage, const double* rho, const double* u, void* dst,
                     const LBArgs& a, int uniform, double urho, const double* uvec,
                     cudaStream_t s);
+// viscous stress (Eq. [viscstress]) of the current state, FP64 dense
+// components 3 half .. 3 half + 2 of (xx, yy, zz, xy, yz, xz)
+void launch_stress(int storage, const void* fstar, const LBArgs& a, int half, double* out,
+                   cudaStream_t s);
 // fluid invariants: partial sums per block then one final block.
 // out[0] = sum of density deviations, out[1..3] = physical momentum,
 // out[4] = number of non-finite densities

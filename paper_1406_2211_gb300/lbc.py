@@ -88,6 +88,7 @@ _PROTOS = {
     "lbc_box_step": (_S, [_P, C.c_int64, _P]),
     "lbc_box_get_fields": (_S, [_P, _P, _P, _P]),
     "lbc_box_get_particles": (_S, [_P, _P, _P, _P, _P]),
+    "lbc_box_get_stress": (_S, [_P, _P, _P]),
     "lbc_box_invariants": (_S, [_P, _P, _P, _P]),
     "lbc_box_status": (_S, [_P]),
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
@@ -319,6 +320,13 @@ class Box:
         check(self.lib.lbc_box_get_fields(self.handle, _ptr(rho), _ptr(u), self._s()),
               "lbc_box_get_fields")
         return rho, u
+
+    def get_stress(self):
+        """Viscous stress sigma[6][nz][ny][nx] (xx, yy, zz, xy, yz, xz)."""
+        sig = np.empty((6,) + self.shape)
+        check(self.lib.lbc_box_get_stress(self.handle, _ptr(sig), self._s()),
+              "lbc_box_get_stress")
+        return sig
 
     def get_particles(self):
         n = self.nparticles
