@@ -63,6 +63,7 @@ struct Layout {
   size_t off_key[2], off_idx[2], off_hist, off_tb, off_te, off_rec;
   size_t off_nbr_start, off_nbr_j, off_nbr_kr, off_nbr_r0sq;
   size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
+  size_t off_home, off_sortflags;     // home tile per marker; {need, changed} per step parity
   size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
   // rigid bodies (at most one per marker)
   size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
@@ -125,6 +126,8 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_mark = take((size_t)L.ntiles * 4);
     L.off_live = take((size_t)L.ntiles * 16);
     L.off_nlive = take(2 * sizeof(int));
+    L.off_home = take((size_t)M * 4);
+    L.off_sortflags = take(4 * sizeof(int));
     // the coupled sub-steps of the multistep split reuse the node moments
     const bool multistep = c->kind != LBC_IBM && c->order == 2 && c->split == LBC_SPLIT_INSIDE &&
                            c->substeps > 1;
@@ -159,7 +162,7 @@ struct lbc_box {
   int cur;          // population array holding the current stored state
   int ia;           // force field holding F_a (pending closing-half force)
   int pc;           // particle position / velocity buffer holding the state
-  bool sorted;      // sorted tile order matches the current positions
+  bool binned;      // markers were sorted into tiles since the last set_particles
   bool steady;      // at least one step done (graphs capture steady state)
   int use_graphs;
   cudaGraphExec_t graph[2];   // two-step graphs, by starting parity of cur
@@ -261,6 +264,7 @@ struct Plan {
   // recorded in b->deferred for a batched launch; 2: the part after it
   int phase = 0;
   bool after_lb = false;
+  int par = 0;     // step parity (the population buffer at the start of the step)
   bool on() const { return phase == 0 || (phase == 1) != after_lb; }
 
   void lb(const void* Fa, const void* Fb, double ca, double cb, double cg) {
@@ -316,8 +320,15 @@ struct Plan {
     d.pos_out = write ? b->dptr(b->L.off_pos[1 - b->pc]) : nullptr;
     d.vel_out = write ? b->dptr(b->L.off_vel[1 - b->pc]) : nullptr;
     d.fint_out = force ? static_cast<void*>(b->arena + b->L.off_fint) : nullptr;
-    d.key_out = b->uptr(b->L.off_key[0]);
-    d.idx_out = b->uptr(b->L.off_idx[0]);
+    d.key_out = b->uptr(b->L.off_key[1]);
+    d.idx_out = b->uptr(b->L.off_idx[1]);
+    if (key) {
+      d.home = b->binned ? b->uptr(b->L.off_home) : nullptr;
+      d.need = need_flag();
+      d.clear_flags = b->iptr(b->L.off_sortflags) + 2 * (1 - par);
+      // no bins yet: this step sorts
+      if (!b->binned) cudaMemsetAsync(d.need, 1, sizeof(int), s);
+    }
     d.inv_mass = b->dptr(b->L.off_inv_mass);
     d.ext = b->arena + b->L.off_ext;
     d.nbr_start = b->iptr(b->L.off_nbr_start);
@@ -342,25 +353,26 @@ struct Plan {
     }
     launch_drift(part_args(b), d, s);
     if (write) b->pc = 1 - b->pc;
-    if (key) b->sorted = false;
     ++n;
   }
 
+  // sort the keys written by the last key-writing drift into tiles, if
+  // that drift found a marker outside its bin (or there are no bins yet)
   void sort() {
     if (!on()) return;
     const int kb = key_bits(b->L.ntiles);
-    launch_sort(b->M, kb, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
-                b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), s);
-    if (b->M > 1) {
-      int passes = (kb + 7) / 8;
-      if (passes & 1) ++passes;
-      n += 3 * passes;
-    }
-    launch_tile_ranges(b->L.ntiles, b->M, b->uptr(b->L.off_key[0]), b->iptr(b->L.off_tb),
-                       b->iptr(b->L.off_te), s);
-    ++n;
-    b->sorted = true;
+    int* need = need_flag();
+    launch_sort(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
+                b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->uptr(b->L.off_key[1]),
+                b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), need, s);
+    launch_bins(b->L.ntiles, b->M, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
+                b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home), need,
+                changed_flag(), s);
+    if (b->M > 0) n += 3 * sort_passes(kb) + 2;
+    b->binned = true;
   }
+  int* need_flag() { return b->iptr(b->L.off_sortflags) + 2 * par; }
+  int* changed_flag() { return b->iptr(b->L.off_sortflags) + 2 * par + 1; }
 
   GatherArgs gather_base() {
     GatherArgs a{};
@@ -430,6 +442,9 @@ struct Plan {
 void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) {
   Plan P{b, s};
   P.phase = phase;
+  // step parity: the population buffer at the start of the step (a phase-2
+  // pass runs after its phase 1 flipped it)
+  P.par = phase == 2 ? 1 - b->cur : b->cur;
   const double h = 1.0;
   const int kind = b->cpl.kind;
   if (!particles(b)) {
@@ -533,9 +548,13 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
         }
         GatherArgs a = P.gather_base();
         a.mode = GM_COUPLE; a.s = make_real(dt); a.include_int = 1; a.rec_weight = make_real(1.0 / n);
-        // the populations and the fixed field are the same for the n
-        // sub-steps of a half: node moments are stored at the first one
-        if (b->L.use_ncache) a.cache = k == 0 ? 1 : 2;
+        // node moments are cached at the first sub-step after the LB step
+        // and reused until the next one (the first half of the next step
+        // sees the same populations), unless a sort moved the slots
+        if (b->L.use_ncache) {
+          a.cache = (half == 1 && k == 0) ? 1 : 2;
+          if (half == 0 && k == 0) a.invalidate = P.changed_flag();
+        }
         const double gfrac = 0.5 * h * double(k) / n;
         if (half == 0)
           P.fields(a, ia, 0.5 * h, k > 0 ? ib : -1, 0.5 * h, 0.5 * h + gfrac);
@@ -552,7 +571,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     // [P F_int P]^n F_h^1/2
     const int n = b->cpl.substeps;
     const double dt = 0.5 * h / n;
-    if (!b->sorted) {
+    if (!b->binned) {
       P.drift(0.0, 0.0, 0.0, false, true, false);
       P.sort();
     }
@@ -601,7 +620,7 @@ lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
       own = true;
     }
     const int cur0 = b->cur, ia0 = b->ia, pc0 = b->pc;
-    const bool sorted0 = b->sorted;
+    const bool binned0 = b->binned;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     b->capturing = true;
     b->lb_in_capture = 0;
@@ -612,7 +631,7 @@ lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (own) cudaStreamDestroy(cs);
     if (e != cudaSuccess) return LBC_ERR_CUDA;
-    if (b->cur != cur0 || b->ia != ia0 || b->pc != pc0 || b->sorted != sorted0) {
+    if (b->cur != cur0 || b->ia != ia0 || b->pc != pc0 || b->binned != binned0) {
       cudaGraphDestroy(graph);
       return LBC_ERR_STATE;
     }
@@ -683,6 +702,15 @@ void free_timing(lbc_box* b) {
   }
   b->timing_cap = 0;
   b->timing_used = 0;
+}
+
+// the populations were replaced from outside a step: node moments cached
+// for the next step's first half are stale
+void populations_changed(lbc_box* b, cudaStream_t s) {
+  if (!b->L.has_particles) return;
+  int* f = b->iptr(b->L.off_sortflags);
+  cudaMemsetAsync(f + 1, 1, sizeof(int), s);
+  cudaMemsetAsync(f + 3, 1, sizeof(int), s);
 }
 
 lbc_status clear_pending(lbc_box* b, cudaStream_t s) {
@@ -814,7 +842,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->maxB = max_bonds;
   b->M = 0;
   b->cur = 0; b->ia = 0; b->pc = 0;
-  b->sorted = false; b->steady = false;
+  b->binned = false; b->steady = false;
   b->use_graphs = 1;
   b->graph[0] = b->graph[1] = nullptr;
   b->tgraph[0] = b->tgraph[1] = nullptr;
@@ -838,7 +866,8 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b->arena + L.off_mark, 0, (size_t)L.ntiles * 4) != cudaSuccess ||
-        cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(b->arena + L.off_sortflags, 0, 4 * sizeof(int)) != cudaSuccess) {
       delete b;
       return LBC_ERR_CUDA;
     }
@@ -868,6 +897,7 @@ lbc_status lbc_box_destroy(lbc_box* b) {
 lbc_status lbc_box_init_equilibrium(lbc_box* b, double rho, const double u[3], void* stream) {
   if (!b || !(rho > 0.0)) return LBC_ERR_ARG;
   if (b->batch) return LBC_ERR_STATE;     // members change only between batches
+  populations_changed(b, S(stream));
   cudaStream_t s = S(stream);
   void* spare = b->pop(1 - b->cur);
   launch_init_eq(b->lat.storage, nullptr, nullptr, spare, b->lb, 1, rho, u, s);
@@ -881,6 +911,7 @@ lbc_status lbc_box_init_equilibrium(lbc_box* b, double rho, const double u[3], v
 lbc_status lbc_box_set_fields(lbc_box* b, const double* rho, const double* u, void* stream) {
   if (!b || !rho || !u) return LBC_ERR_ARG;
   if (b->batch) return LBC_ERR_STATE;     // members change only between batches
+  populations_changed(b, S(stream));
   cudaStream_t s = S(stream);
   const Geom& g = b->L.g;
   const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -903,6 +934,7 @@ lbc_status lbc_box_set_fields(lbc_box* b, const double* rho, const double* u, vo
 lbc_status lbc_box_set_populations(lbc_box* b, const double* f, void* stream) {
   if (!b || !f) return LBC_ERR_ARG;
   if (b->batch) return LBC_ERR_STATE;     // members change only between batches
+  populations_changed(b, S(stream));
   cudaStream_t s = S(stream);
   lbc_status st;
   switch (b->lat.storage) {
@@ -1087,7 +1119,8 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   b->nrigid = B;
   b->rigid_k = B > 0 ? p->rigid_k : 0.0;
   b->rigid_krep = B > 0 ? p->rigid_repulsion_k : 0.0;
-  b->sorted = false;
+  CK(cudaMemsetAsync(b->iptr(b->L.off_sortflags), 0, 4 * sizeof(int), s));
+  b->binned = false;
   reset_graphs(b);
   CK(cudaStreamSynchronize(s));
   return LBC_OK;
@@ -1364,10 +1397,10 @@ lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     own = true;
   }
-  struct Saved { int cur, ia, pc; bool sorted; };
+  struct Saved { int cur, ia, pc; bool binned; };
   std::vector<Saved> saved;
   for (const auto& m : B->members)
-    saved.push_back({m.box->cur, m.box->ia, m.box->pc, m.box->sorted});
+    saved.push_back({m.box->cur, m.box->ia, m.box->pc, m.box->binned});
   std::vector<BoxEntry> host[2];
   int64_t l = 0;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -1385,7 +1418,7 @@ lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
   for (size_t j = 0; j < B->members.size(); ++j) {
     const lbc_box* b = B->members[j].box;
     const Saved& v = saved[j];
-    if (b->cur != v.cur || b->ia != v.ia || b->pc != v.pc || b->sorted != v.sorted) {
+    if (b->cur != v.cur || b->ia != v.ia || b->pc != v.pc || b->binned != v.binned) {
       cudaGraphDestroy(graph);
       return LBC_ERR_STATE;
     }

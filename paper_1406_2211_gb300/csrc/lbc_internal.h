@@ -131,18 +131,30 @@ struct DriftArgs {
   const void* nbr_kr;                            // (k, r0) per entry, compute type
   const double* nbr_r0sq;                        // r0^2 per entry
   RigidArgs rigid;                               // nbodies == 0: no rigid bodies
+  // binning (write_key): home tile of each marker at the last sort (null:
+  // no sort yet), the flag that requests a sort this step, and the two
+  // flags of the previous step to clear
+  const uint32_t* home;
+  int* need;
+  int* clear_flags;
 };
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
 // frames and repulsion of the rigid bodies at the pre-drifted positions of
 // a drift with compute_force (launched before it)
 void launch_rigid_frames(const PartArgs& p, const DriftArgs& d, cudaStream_t s);
 
-// LSD radix sort of (key, idx) pairs; ping-pong buffers, result in *_a
+// LSD radix sort of (key, idx) pairs from (kin, vin), result in (ka, va),
+// (kb, vb) scratch (may alias kin, vin); nothing runs when *need == 0
 size_t sort_scratch_ints(long long M);
-void launch_sort(long long M, int key_bits, uint32_t* key_a, uint32_t* idx_a,
-                 uint32_t* key_b, uint32_t* idx_b, int* hist, cudaStream_t s);
-void launch_tile_ranges(int ntiles, long long M, const uint32_t* sorted_keys,
-                        int* tile_begin, int* tile_end, cudaStream_t s);
+int sort_passes(int key_bits);
+void launch_sort(long long M, int key_bits, const uint32_t* kin, const uint32_t* vin, uint32_t* ka,
+                 uint32_t* va, uint32_t* kb, uint32_t* vb, int* hist, const int* need,
+                 cudaStream_t s);
+// tile ranges, home tiles and the "bins changed" flag after a sort (same
+// condition)
+void launch_bins(int ntiles, long long M, const uint32_t* sorted_keys, const uint32_t* idx,
+                 int* tile_begin, int* tile_end, uint32_t* home, const int* need, int* changed,
+                 cudaStream_t s);
 
 enum GatherMode {
   GM_COUPLE = 0,      // force coupling / EBF / modified EBF half step
@@ -170,11 +182,12 @@ struct GatherArgs {
   const void* F2; const uint8_t* flag2; Real c2;
   Real cgg[3];          // cg g
   Real rho0_pop;
-  // per-slot cache of j + c1 F1 and 1 / rho at the stencil nodes, valid
-  // while pops and F1 are unchanged: 0 unused, 1 store, 2 reuse where the
-  // slot's stencil base is the stored one.  Layout [(node * 4 + c) * M + k];
-  // ncache_b[k] holds the base it was taken at.
+  // per-slot cache of j and 1 / rho at the stencil nodes, valid while the
+  // populations and the binning are unchanged: 0 unused, 1 store, 2 reuse
+  // where the slot's stencil base is the stored one.  Layout
+  // [node][slot] of 4 values; ncache_b[k] holds the base it was taken at.
   int cache; void* ncache; int4* ncache_b;
+  const int* invalidate;          // reuse only while *invalidate == 0 (null: no check)
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
   const uint32_t* keys;           // sorted home tile of each slot (null: no check)

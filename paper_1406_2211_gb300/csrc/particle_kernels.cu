@@ -199,6 +199,32 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
   if (d.write_key) {
     d.key_out[i] = key_of(g, r2[0], r2[1], r2[2]);
     d.idx_out[i] = (uint32_t)i;
+    if (i == 0 && d.clear_flags) {       // the flags of the previous step
+      d.clear_flags[0] = 0;
+      d.clear_flags[1] = 0;
+    }
+    if (d.home) {
+      // markers keep their bins while they are within half a cell of their
+      // home tile: over the step they then stay within the one cell the
+      // spreading's neighbour search allows (they move far less than half
+      // a cell per step); otherwise the step re-sorts
+      const int t = (int)d.home[i];
+      const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+      bool inside = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int lo = tt[c] * TILE, w = min(lo + TILE, n3[c]) - lo;
+        if (per[c] && n3[c] <= 3 * TILE) continue;      // the search covers the axis
+        double dd = r2[c] - (double)lo;
+        if (per[c]) {
+          const double h = 0.5 * n3[c];
+          if (dd < -h) dd += n3[c];
+          else if (dd >= h) dd -= n3[c];
+        }
+        inside = inside && dd >= -0.5 && dd < (double)w + 0.5;
+      }
+      if (!inside) *d.need = 1;
+    }
   }
 }
 
@@ -354,10 +380,14 @@ void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ radix sort
-// Stable LSD radix sort, 8-bit digits.  Each block owns SORT_BLOCK
-// consecutive elements; per-block digit counts, one exclusive scan over
-// (digit, block), and a stable scatter that ranks equal digits in element
-// order (warp match within rounds of 256 elements).
+// Stable LSD radix sort with digits of at most 8 bits.  Each block owns
+// SORT_BLOCK consecutive elements; per-block digit counts, one exclusive
+// scan over (digit, block), and a stable scatter that ranks equal digits in
+// element order (warp match within rounds of 256 elements).  The number of
+// passes is odd, so the keys written to the b buffers end up sorted in the
+// a buffers, which keep the previous result when the sort is skipped.
+// Every kernel of the sort returns at once when *need == 0 (the markers are
+// still in their bins, see the drift).
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_BLOCK = SORT_THREADS * SORT_ITEMS;
@@ -366,15 +396,19 @@ static int sort_blocks(long long M) { return (int)((M + SORT_BLOCK - 1) / SORT_B
 
 size_t sort_scratch_ints(long long M) { return (size_t)256 * (size_t)sort_blocks(M > 0 ? M : 1) + 256; }
 
+__device__ inline bool skip(const int* need) { return need != nullptr && *need == 0; }
+
 __global__ void __launch_bounds__(SORT_THREADS)
-sort_hist_kernel(const uint32_t* __restrict__ keys, long long M, int shift, int* hist, int nblocks) {
+sort_hist_kernel(const uint32_t* __restrict__ keys, long long M, int shift, uint32_t mask, int* hist,
+                 int nblocks, const int* need) {
+  if (skip(need)) return;
   __shared__ int cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * SORT_BLOCK;
   for (int r = 0; r < SORT_ITEMS; ++r) {
     const long long e = base + r * SORT_THREADS + threadIdx.x;
-    if (e < M) atomicAdd(&cnt[(keys[e] >> shift) & 255u], 1);   // shared, integer
+    if (e < M) atomicAdd(&cnt[(keys[e] >> shift) & mask], 1);   // shared, integer
   }
   __syncthreads();
   hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
@@ -382,7 +416,8 @@ sort_hist_kernel(const uint32_t* __restrict__ keys, long long M, int shift, int*
 
 // exclusive scan of n ints in place, one block of 1024 threads: each thread
 // sums a contiguous chunk, the chunk sums are scanned with warp shuffles
-__global__ void __launch_bounds__(1024) scan_kernel(int* data, int n) {
+__global__ void __launch_bounds__(1024) scan_kernel(int* data, int n, const int* need) {
+  if (skip(need)) return;
   __shared__ int wsum[32];
   const int per = (n + 1023) / 1024;
   const int lo = threadIdx.x * per;
@@ -422,7 +457,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(int* data, int n) {
 __global__ void __launch_bounds__(SORT_THREADS)
 sort_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, long long M, int shift,
-                    const int* __restrict__ hist, int nblocks) {
+                    uint32_t mask, const int* __restrict__ hist, int nblocks, const int* need) {
+  if (skip(need)) return;
   constexpr int W = SORT_THREADS / 32;
   __shared__ int base_cnt[256];          // elements of each digit already placed
   __shared__ int wcnt[W][256];           // this round: count per warp and digit
@@ -435,7 +471,7 @@ sort_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict
     const long long e = base + r * SORT_THREADS + threadIdx.x;
     const bool valid = e < M;
     const uint32_t key = valid ? kin[e] : 0u;
-    const int dig = valid ? (int)((key >> shift) & 255u) : 256;
+    const int dig = valid ? (int)((key >> shift) & mask) : 256;
     const unsigned peers = __match_any_sync(0xffffffffu, dig);
     const int rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
@@ -457,55 +493,73 @@ sort_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict
   }
 }
 
-void launch_sort(long long M, int key_bits, uint32_t* ka, uint32_t* va, uint32_t* kb,
-                 uint32_t* vb, int* hist, cudaStream_t s) {
-  if (M <= 1) return;
-  const int nb = sort_blocks(M);
+int sort_passes(int key_bits) {
   int passes = (key_bits + 7) / 8;
   if (passes < 1) passes = 1;
-  // an odd number of passes ends in the b buffers; add one copy pass by
-  // sorting on an empty digit so the result always lands in a
-  if (passes & 1) passes += 1;
-  uint32_t *k0 = ka, *v0 = va, *k1 = kb, *v1 = vb;
+  if (!(passes & 1)) passes += 1;
+  return passes;
+}
+
+void launch_sort(long long M, int key_bits, const uint32_t* kin, const uint32_t* vin, uint32_t* ka,
+                 uint32_t* va, uint32_t* kb, uint32_t* vb, int* hist, const int* need,
+                 cudaStream_t s) {
+  if (M <= 0) return;
+  const int nb = sort_blocks(M);
+  const int passes = sort_passes(key_bits);
+  const int width = (key_bits + passes - 1) / passes;     // <= 8
+  const uint32_t mask = (1u << width) - 1u;
+  // pass p reads the b buffers when p is even and writes a (odd: a -> b);
+  // the first pass reads the given input
+  const uint32_t* k0 = kin;
+  const uint32_t* v0 = vin;
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    sort_hist_kernel<<<nb, SORT_THREADS, 0, s>>>(k0, M, shift, hist, nb);
-    scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * nb);
-    sort_scatter_kernel<<<nb, SORT_THREADS, 0, s>>>(k0, v0, k1, v1, M, shift, hist, nb);
-    uint32_t* t;
-    t = k0; k0 = k1; k1 = t;
-    t = v0; v0 = v1; v1 = t;
+    uint32_t* k1 = (p & 1) ? kb : ka;
+    uint32_t* v1 = (p & 1) ? vb : va;
+    const int shift = width * p;
+    sort_hist_kernel<<<nb, SORT_THREADS, 0, s>>>(k0, M, shift, mask, hist, nb, need);
+    scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * nb, need);
+    sort_scatter_kernel<<<nb, SORT_THREADS, 0, s>>>(k0, v0, k1, v1, M, shift, mask, hist, nb, need);
+    k0 = k1;
+    v0 = v1;
   }
 }
 
-__global__ void tile_ranges_kernel(int ntiles, long long M, const uint32_t* __restrict__ keys,
-                                   int* __restrict__ tb, int* __restrict__ te) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  // lower bounds of t and t + 1 in the sorted keys
-  long long lo = 0, hi = M;
-  while (lo < hi) {
-    const long long mid = (lo + hi) >> 1;
-    if (keys[mid] < (uint32_t)t) lo = mid + 1; else hi = mid;
+// after a sort: tile ranges [tb, te) of the sorted keys (tiles without
+// markers get an empty range), the home tile of every marker, and the
+// "bins changed" flag
+__global__ void bins_clear_kernel(int ntiles, int* __restrict__ tb, int* __restrict__ te,
+                                  const int* need) {
+  if (skip(need)) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    tb[t] = 0;
+    te[t] = 0;
   }
-  const long long b = lo;
-  hi = M;
-  while (lo < hi) {
-    const long long mid = (lo + hi) >> 1;
-    if (keys[mid] < (uint32_t)t + 1u) lo = mid + 1; else hi = mid;
-  }
-  tb[t] = (int)b;
-  te[t] = (int)lo;
 }
 
-void launch_tile_ranges(int ntiles, long long M, const uint32_t* keys, int* tb, int* te,
-                        cudaStream_t s) {
-  const int bs = 256;
-  tile_ranges_kernel<<<(ntiles + bs - 1) / bs, bs, 0, s>>>(ntiles, M, keys, tb, te);
+__global__ void bins_kernel(long long M, const uint32_t* __restrict__ keys,
+                            const uint32_t* __restrict__ idx, int* __restrict__ tb,
+                            int* __restrict__ te, uint32_t* __restrict__ home, const int* need,
+                            int* changed) {
+  if (skip(need)) return;
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k == 0 && changed) *changed = 1;
+  if (k >= M) return;
+  const uint32_t t = keys[k];
+  if (k == 0 || keys[k - 1] != t) tb[t] = (int)k;
+  if (k == M - 1 || keys[k + 1] != t) te[t] = (int)(k + 1);
+  home[idx[k]] = t;
+}
+
+void launch_bins(int ntiles, long long M, const uint32_t* keys, const uint32_t* idx, int* tb,
+                 int* te, uint32_t* home, const int* need, int* changed, cudaStream_t s) {
+  bins_clear_kernel<<<(ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024, 256, 0, s>>>(
+      ntiles, tb, te, need);
+  if (M > 0) bins_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(M, keys, idx, tb, te, home, need,
+                                                                     changed);
 }
 
 // ------------------------------------------------------------ gather + couple
-// j + c1 F1 (F1 where its tile flag is set) and 1 / rho at node (x, y, z)
+// j and 1 / rho at node (x, y, z)
 template <typename S, bool WALLS>
 __device__ inline void node_base(const GatherArgs& a, const Geom& g, int x, int y, int z,
                                  typename Store<S>::C (&j)[3], typename Store<S>::C& inv) {
@@ -520,12 +574,6 @@ __device__ inline void node_base(const GatherArgs& a, const Geom& g, int x, int 
     if (cx_of(i)) j0 += C(cx_of(i)) * v;
     if (cy_of(i)) j1 += C(cy_of(i)) * v;
     if (cz_of(i)) j2 += C(cz_of(i)) * v;
-  }
-  const C* F1 = static_cast<const C*>(a.F1);
-  if (F1 && a.flag1[tile_of(g, x, y, z)]) {
-    const long long cell = z * g.plane + (long long)y * g.pitch + x;
-    const C c1 = rv<C>(a.c1);
-    j0 += c1 * F1[cell]; j1 += c1 * F1[g.qstride + cell]; j2 += c1 * F1[2 * g.qstride + cell];
   }
   j[0] = j0; j[1] = j1; j[2] = j2;
   inv = C(1) / (rv<C>(a.rho0_pop) + rd);
@@ -569,8 +617,8 @@ __device__ inline void cache_store(double* p, const double (&j)[3], double inv) 
 }
 
 // fluid velocity at one stencil node (x, y, z) of weight wt, added to own:
-// ((j + c1 F1) + cg g + c2 F2) / rho, with j + c1 F1 and 1 / rho taken from
-// the node cache where it is valid
+// (((j + c1 F1) + cg g) + c2 F2) / rho, with j and 1 / rho taken from the
+// node cache where it is valid (F1, F2 where their tile flags are set)
 template <typename S, bool WALLS>
 __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, int x, int y, int z,
                                             typename Store<S>::C wt, bool reuse,
@@ -585,10 +633,16 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
     node_base<S, WALLS>(a, g, x, y, z, j, inv);
     if (a.cache != 0) cache_store(slot, j, inv);
   }
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  const int tile = tile_of(g, x, y, z);
+  const C* F1 = static_cast<const C*>(a.F1);
+  if (F1 && a.flag1[tile]) {
+    const C c1 = rv<C>(a.c1);
+    j[0] += c1 * F1[cell]; j[1] += c1 * F1[g.qstride + cell]; j[2] += c1 * F1[2 * g.qstride + cell];
+  }
   j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
   const C* F2 = static_cast<const C*>(a.F2);
-  if (F2 && a.flag2[tile_of(g, x, y, z)]) {
-    const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  if (F2 && a.flag2[tile]) {
     const C c2 = rv<C>(a.c2);
     j[0] += c2 * F2[cell]; j[1] += c2 * F2[g.qstride + cell]; j[2] += c2 * F2[2 * g.qstride + cell];
   }
@@ -655,7 +709,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
     const C cgg[3] = {rv<C>(a.cgg[0]), rv<C>(a.cgg[1]), rv<C>(a.cgg[2])};
     C* nc = static_cast<C*>(a.ncache);
     bool reuse = false;
-    if (a.cache == 2) {
+    if (a.cache == 2 && (a.invalidate == nullptr || *a.invalidate == 0)) {
       const int4 cb = a.ncache_b[k];
       reuse = cb.x == b[0] && cb.y == b[1] && cb.z == b[2];
     }
