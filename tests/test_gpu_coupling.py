@@ -181,3 +181,29 @@ def test_cfg2_reduced_mrt_chains():
     _, u = box.get_fields()
     assert rel_l2(u, sm.fluid_velocity()) < 1e-5
     box.close()
+
+
+def test_fast_markers_are_rebinned_in_graph_replays():
+    """Markers moving 0.3 cells per step leave their 4^3 bins every few
+    steps; the re-sorts then happen inside replayed graphs (device-side
+    decision).  FP64 storage: trajectories equal the oracle's to roundoff."""
+    require_cuda()
+    shape = (16, 20, 24)
+    rng = np.random.default_rng(12)
+    M = 40
+    pos = rng.uniform(0, 1, (M, 3)) * [24, 20, 16]
+    vel = np.tile([0.3, -0.2, 0.1], (M, 1)) + 0.02 * rng.standard_normal((M, 3))
+    parts = dict(pos=pos, vel=vel, mass=50.0)
+    fbar0 = synth.random_populations(shape, seed=3, amp=1e-4)
+    box, sm = make_pair(shape, fbar0, tau=0.9, storage="f64", kind="fc", order=2,
+                        stencil="trilinear", gamma=0.05, parts=parts)
+    steps = 40
+    for _ in range(steps):
+        sm.step()
+    box.step(steps)
+    p, v, _ = box.get_particles()
+    assert np.abs(OC.min_image(p - sm.parts.pos, shape, False)).max() < 1e-11
+    assert np.abs(v - sm.parts.vel).max() < 1e-12
+    assert box.status() == 0
+    disp = np.abs(OC.min_image(sm.parts.pos - OC.wrap_positions(pos, shape, False), shape, False))
+    assert disp.max() > 8.0                     # markers crossed several bins
