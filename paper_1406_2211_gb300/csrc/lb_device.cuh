@@ -68,6 +68,30 @@ template <> struct Store<__nv_bfloat16> {
   }
 };
 
+// Force fields: one 4-vector (x, y, z, unused) per cell in the compute
+// type, so a cell's force is one 16-byte (float) or two 16-byte (double)
+// accesses.
+template <typename IX>
+__device__ inline void load_force(const float* F, IX cell, float& x, float& y, float& z) {
+  const float4 v = reinterpret_cast<const float4*>(F)[cell];
+  x = v.x; y = v.y; z = v.z;
+}
+template <typename IX>
+__device__ inline void load_force(const double* F, IX cell, double& x, double& y, double& z) {
+  const double2 v0 = reinterpret_cast<const double2*>(F)[2 * cell];
+  const double2 v1 = reinterpret_cast<const double2*>(F)[2 * cell + 1];
+  x = v0.x; y = v0.y; z = v1.x;
+}
+template <typename IX>
+__device__ inline void store_force(float* F, IX cell, float x, float y, float z) {
+  reinterpret_cast<float4*>(F)[cell] = make_float4(x, y, z, 0.0f);
+}
+template <typename IX>
+__device__ inline void store_force(double* F, IX cell, double x, double y, double z) {
+  reinterpret_cast<double2*>(F)[2 * cell] = make_double2(x, y);
+  reinterpret_cast<double2*>(F)[2 * cell + 1] = make_double2(z, 0.0);
+}
+
 // Random bits for the stochastic rounding of the values of one cell: a seed
 // from the cell index and one of the cell's own values (so the draws change
 // from step to step, and the same inputs give the same bits), then a short

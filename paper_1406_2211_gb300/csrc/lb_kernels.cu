@@ -184,15 +184,19 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
     const C* Fb = static_cast<const C*>(a.Fb);
     if (Fa && a.flag_a[t]) {
       const C ca = rv<C>(a.ca);
-      Fx += ca * Fa[cell];
-      Fy += ca * Fa[qs + cell];
-      Fz += ca * Fa[2 * qs + cell];
+      C fx, fy, fz;
+      load_force(Fa, cell, fx, fy, fz);
+      Fx += ca * fx;
+      Fy += ca * fy;
+      Fz += ca * fz;
     }
     if (Fb && a.flag_b[t]) {
       const C cb = rv<C>(a.cb);
-      Fx += cb * Fb[cell];
-      Fy += cb * Fb[qs + cell];
-      Fz += cb * Fb[2 * qs + cell];
+      C fx, fy, fz;
+      load_force(Fb, cell, fx, fy, fz);
+      Fx += cb * fx;
+      Fy += cb * fy;
+      Fz += cb * fz;
     }
   }
   const C u1x = u0x + Fx * inv, u1y = u0y + Fy * inv, u1z = u0z + Fz * inv;
@@ -477,9 +481,11 @@ __global__ void fields_kernel(const S* __restrict__ fstar, const LBArgs a, doubl
   const int t = tile_of(g, x, y, z);
   const C* Fa = static_cast<const C*>(a.Fa);
   const bool fa = Fa != nullptr && a.flag_a[t];
+  C fv[3] = {C(0), C(0), C(0)};
+  if (fa) load_force(Fa, cell, fv[0], fv[1], fv[2]);
   for (int c = 0; c < 3; ++c) {
     double jj = j[c] + cg * a.gvec[c];
-    if (fa) jj += ca * double(Fa[c * g.qstride + cell]);
+    if (fa) jj += ca * double(fv[c]);
     u_out[c * N + dense] = jj / rho;
   }
   rho_out[dense] = rho;
@@ -579,9 +585,11 @@ invariants_kernel(const S* __restrict__ fstar, const LBArgs a, double ca, double
       const int t = tile_of(g, x, y, z);
       const C* Fa = static_cast<const C*>(a.Fa);
       if (Fa != nullptr && a.flag_a[t]) {
-        j0 += ca * double(Fa[cell]);
-        j1 += ca * double(Fa[g.qstride + cell]);
-        j2 += ca * double(Fa[2 * g.qstride + cell]);
+        C fx, fy, fz;
+        load_force(Fa, cell, fx, fy, fz);
+        j0 += ca * double(fx);
+        j1 += ca * double(fy);
+        j2 += ca * double(fz);
       }
       j0 += cg * a.gvec[0]; j1 += cg * a.gvec[1]; j2 += cg * a.gvec[2];
       acc[0] += rd; acc[1] += j0; acc[2] += j1; acc[3] += j2;

@@ -94,7 +94,8 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
   L.pop_bytes = (size_t)Q * (size_t)g.qstride * L.esize;
   L.off_pop[0] = take(L.pop_bytes);
   L.off_pop[1] = take(L.pop_bytes);
-  const size_t fbytes = 3 * (size_t)g.qstride * force_elem_bytes(l->storage);
+  // force fields: a 4-vector (x, y, z, unused) per cell
+  const size_t fbytes = 4 * (size_t)g.qstride * force_elem_bytes(l->storage);
   if (L.has_particles) {
     L.off_F[0] = take(fbytes); L.off_F[1] = take(fbytes);
     L.off_flag[0] = take(L.ntiles); L.off_flag[1] = take(L.ntiles);
@@ -969,13 +970,13 @@ lbc_status lbc_box_set_pending_force(lbc_box* b, const double* Fa, void* stream)
   const Geom& g = b->L.g;
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const bool dbl = b->lat.storage == LBC_F64;
-  std::vector<double> hd(dbl ? 3 * (size_t)g.qstride : 0, 0.0);
-  std::vector<float> hf(dbl ? 0 : 3 * (size_t)g.qstride, 0.0f);
+  std::vector<double> hd(dbl ? 4 * (size_t)g.qstride : 0, 0.0);
+  std::vector<float> hf(dbl ? 0 : 4 * (size_t)g.qstride, 0.0f);
   for (int c = 0; c < 3; ++c)
     for (int z = 0; z < g.nz; ++z)
       for (int y = 0; y < g.ny; ++y)
         for (int x = 0; x < g.nx; ++x) {
-          const size_t at = (size_t)c * g.qstride + (size_t)z * g.plane + (size_t)y * g.pitch + x;
+          const size_t at = 4 * ((size_t)z * g.plane + (size_t)y * g.pitch + x) + (size_t)c;
           const double v = Fa[(size_t)c * N + ((size_t)z * g.ny + y) * g.nx + x];
           if (dbl) hd[at] = v; else hf[at] = (float)v;
         }

@@ -23,9 +23,9 @@ struct LBArgs {
   double gvec[3];         // uniform body force density g
   Real bb_bot[Q];         // moving-wall term of population i arriving from
   Real bb_top[Q];         //   the bottom / top wall: 6 w_i rho0 c_i . u_w
-  // sparse force fields (may be null): F[c * qstride + cell] in the compute
-  // type of the storage (double for FP64 storage, float otherwise), one
-  // activity flag per force tile
+  // sparse force fields (may be null): a 4-vector F[4 cell + c] (c = x, y,
+  // z; the fourth unused) in the compute type of the storage (double for
+  // FP64 storage, float otherwise), one activity flag per force tile
   const void* Fa; const uint8_t* flag_a;
   const void* Fb; const uint8_t* flag_b;
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)

@@ -638,13 +638,17 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
   const C* F1 = static_cast<const C*>(a.F1);
   if (F1 && a.flag1[tile]) {
     const C c1 = rv<C>(a.c1);
-    j[0] += c1 * F1[cell]; j[1] += c1 * F1[g.qstride + cell]; j[2] += c1 * F1[2 * g.qstride + cell];
+    C fx, fy, fz;
+    load_force(F1, cell, fx, fy, fz);
+    j[0] += c1 * fx; j[1] += c1 * fy; j[2] += c1 * fz;
   }
   j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
   const C* F2 = static_cast<const C*>(a.F2);
   if (F2 && a.flag2[tile]) {
     const C c2 = rv<C>(a.c2);
-    j[0] += c2 * F2[cell]; j[1] += c2 * F2[g.qstride + cell]; j[2] += c2 * F2[2 * g.qstride + cell];
+    C fx, fy, fz;
+    load_force(F2, cell, fx, fy, fz);
+    j[0] += c2 * fx; j[1] += c2 * fy; j[2] += c2 * fz;
   }
   own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
 }
@@ -1057,11 +1061,8 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
     const long long cell1 = cell0 + 2 * g.plane;
     C acc0[3] = {C(0), C(0), C(0)}, acc1[3] = {C(0), C(0), C(0)};
     if (a.accumulate && a.flag[t]) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (in0) acc0[c] = F[c * g.qstride + cell0];
-        if (in1) acc1[c] = F[c * g.qstride + cell1];
-      }
+      if (in0) load_force(F, cell0, acc0[0], acc0[1], acc0[2]);
+      if (in1) load_force(F, cell1, acc1[0], acc1[1], acc1[2]);
     }
     // neighbour tiles per axis: lane q < 8 reads entry q of each table row
     int rowv[3], nt[3];
@@ -1150,11 +1151,8 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
         __syncwarp();
       }
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (in0) F[c * g.qstride + cell0] = acc0[c];
-      if (in1) F[c * g.qstride + cell1] = acc1[c];
-    }
+    if (in0) store_force(F, cell0, acc0[0], acc0[1], acc0[2]);
+    if (in1) store_force(F, cell1, acc1[0], acc1[1], acc1[2]);
     if (lane == 0) a.flag[t] = 1;
   }
   // the last block to finish resets the list for the next gather (every
