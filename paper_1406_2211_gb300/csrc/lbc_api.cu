@@ -311,6 +311,15 @@ struct Plan {
   void drift(double pre, double kick, double post, bool force, bool key, bool write = true,
              const double* pos_in = nullptr, double pre0 = 0.0) {
     if (!on()) return;
+    const DriftArgs d = drift_setup(pre, kick, post, force, key, write, pos_in, pre0);
+    launch_drift(part_args(b), d, s);
+    ++n;
+  }
+
+  // the arguments of a drift sub-step (and the launches that must precede
+  // it); flips the particle buffers as the drift will
+  DriftArgs drift_setup(double pre, double kick, double post, bool force, bool key,
+                        bool write = true, const double* pos_in = nullptr, double pre0 = 0.0) {
     DriftArgs d{};
     d.dt_pre0 = pre0;
     d.dt_pre = pre; d.dt_kick = kick; d.dt_post = post;
@@ -352,9 +361,8 @@ struct Plan {
       launch_rigid_frames(part_args(b), d, s);
       n += 2;
     }
-    launch_drift(part_args(b), d, s);
     if (write) b->pc = 1 - b->pc;
-    ++n;
+    return d;
   }
 
   // sort the keys written by the last key-writing drift into tiles, if
@@ -541,13 +549,21 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     for (int half = 0; half < 2; ++half) {
       const int out = half == 0 ? ib : ia;
       for (int k = 0; k < n; ++k) {
+        // the drift of a sub-step runs inside its gather, except the
+        // first one, whose keys the sort needs first
+        DriftArgs fd{};
+        const bool fused = !(half == 0 && k == 0) && P.on();
         if (half == 0 && k == 0) {
           P.drift(0.5 * dt, 0.0, 0.0, true, true);
           P.sort();
-        } else {
-          P.drift(0.5 * dt, 0.0, 0.0, true, false, true, nullptr, 0.5 * dt);
+        } else if (fused) {
+          fd = P.drift_setup(0.5 * dt, 0.0, 0.0, true, false, true, nullptr, 0.5 * dt);
         }
         GatherArgs a = P.gather_base();
+        if (fused) {
+          a.fused = 1;
+          a.drift = fd;
+        }
         a.mode = GM_COUPLE; a.s = make_real(dt); a.include_int = 1; a.rec_weight = make_real(1.0 / n);
         // node moments are cached at the first sub-step after the LB step
         // and reused until the next one (the first half of the next step

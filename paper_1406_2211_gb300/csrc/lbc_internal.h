@@ -188,6 +188,10 @@ struct GatherArgs {
   // [node][slot] of 4 values; ncache_b[k] holds the base it was taken at.
   int cache; void* ncache; int4* ncache_b;
   const int* invalidate;          // reuse only while *invalidate == 0 (null: no check)
+  // fused: the thread of slot k first runs the drift sub-step `drift` of
+  // its marker (mode GM_COUPLE; positions, velocities and F_int come from it)
+  int fused;
+  DriftArgs drift;
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
   const uint32_t* keys;           // sorted home tile of each slot (null: no check)

@@ -108,10 +108,11 @@ __device__ inline uint32_t key_of(const Geom& g, double x, double y, double z) {
 }
 
 // ------------------------------------------------------------ drift / forces
+// One marker's sub-step (see DriftArgs): writes its new position, velocity,
+// intrinsic force and key, and returns the position, velocity and force.
 template <typename C>
-__global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const DriftArgs d) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= p.M) return;
+__device__ __forceinline__ void drift_one(const PartArgs& p, const DriftArgs& d, long long i,
+                                          double (&r2)[3], double (&v)[3], C (&F)[3]) {
   const long long M = p.M;
   const Geom& g = p.g;
   const int n3[3] = {g.nx, g.ny, g.nz};
@@ -119,13 +120,13 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
   // intermediate positions are left unwrapped (they stay within a cell of
   // the box); only the final position is wrapped, and bond vectors use the
   // minimum image, so no FP64 work is spent on wrapping in between
-  double r1[3], v[3];
+  double r1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     v[c] = d.vel_in[c * M + i];
     r1[c] = (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
   }
-  C F[3] = {C(0), C(0), C(0)};
+  F[0] = F[1] = F[2] = C(0);
   if (d.compute_force) {
     const C* ext = static_cast<const C*>(d.ext);
     const C* kr = static_cast<const C*>(d.nbr_kr);
@@ -185,13 +186,16 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
       for (int c = 0; c < 3; ++c) fo[c * M + i] = F[c];
     }
   }
-  const double kick = d.dt_kick * d.inv_mass[i];
-  double r2[3];
+  // (a zero kick or post-drift leaves v and r unchanged: skipped, FP64 work
+  // being scarce)
+  if (d.dt_kick != 0.0) {
+    const double kick = d.dt_kick * d.inv_mass[i];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    v[c] += kick * (double)F[c];
-    r2[c] = wrap_axis(r1[c] + d.dt_post * v[c], n3[c], per[c]);
+    for (int c = 0; c < 3; ++c) v[c] += kick * (double)F[c];
   }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    r2[c] = wrap_axis(d.dt_post != 0.0 ? r1[c] + d.dt_post * v[c] : r1[c], n3[c], per[c]);
   if (d.pos_out)
     for (int c = 0; c < 3; ++c) d.pos_out[c * M + i] = r2[c];
   if (d.vel_out)
@@ -226,6 +230,15 @@ __global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const Drif
       if (!inside) *d.need = 1;
     }
   }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(128) drift_kernel(const PartArgs p, const DriftArgs d) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= p.M) return;
+  double r2[3], v[3];
+  C F[3];
+  drift_one<C>(p, d, i, r2, v, F);
 }
 
 // ------------------------------------------------------------ rigid bodies
@@ -579,14 +592,17 @@ __device__ inline void node_base(const GatherArgs& a, const Geom& g, int x, int 
   inv = C(1) / (rv<C>(a.rho0_pop) + rd);
 }
 
-// is cell c within [lo - 1, hi + 1] of its home tile (periodic wrap)?
-__device__ inline bool near_home(int c, int lo, int hi, int n, bool periodic) {
-  if (!periodic) return c >= lo - 1 && c <= hi + 1;
-  if (n <= 3 * TILE) return true;      // the search window spans the whole axis
-  int d = c - lo;
-  if (d < -n / 2) d += n;
-  else if (d >= n - n / 2) d -= n;
-  return d >= -1 && d <= hi - lo + 1;
+// do the stencil nodes b .. b + SN - 1 lie within [lo - 3, hi + 3] of the
+// home tile (periodic wrap)?
+template <int SN>
+__device__ inline bool stencil_near_home(int b, int lo, int hi, int n, bool periodic) {
+  if (periodic && n <= 3 * TILE) return true;     // the search window spans the axis
+  int d = b - lo;
+  if (periodic) {
+    if (d < -n / 2) d += n;
+    else if (d >= n - n / 2) d -= n;
+  }
+  return d >= -3 && d + SN - 1 <= hi - lo + 3;
 }
 
 // Gather and coupling update, one marker (sorted slot k) per thread.  The
@@ -671,34 +687,43 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
   const int n3[3] = {g.nx, g.ny, g.nz};
   const bool per[3] = {true, true, !g.walls};
 
-  // the particle's own data (independent of the gather)
+  // the particle's own data (independent of the gather); with a fused
+  // drift this thread first does its marker's drift sub-step
   double v[3] = {0.0, 0.0, 0.0};
   double im = 0.0;
   C Fi[3] = {C(0), C(0), C(0)};
-  const C* fint = static_cast<const C*>(a.fint);
-  if (a.mode == GM_COUPLE) {
+  double X[3];
+  const bool at_aux = a.mode == GM_IBM_HALF || a.mode == GM_IBM_FINAL;
+  if (a.fused) {
+    C F[3];
+    drift_one<C>(p, a.drift, i, X, v, F);
     im = a.inv_mass[i];
+    if (a.include_int)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      v[c] = a.vel[c * M + i];
-      if (a.include_int) Fi[c] = fint[c * M + i];
+      for (int c = 0; c < 3; ++c) Fi[c] = F[c];
+  } else {
+    const C* fint = static_cast<const C*>(a.fint);
+    if (a.mode == GM_COUPLE) {
+      im = a.inv_mass[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[c] = a.vel[c * M + i];
+        if (a.include_int) Fi[c] = fint[c * M + i];
+      }
+    } else if (a.mode == GM_IBM_HALF || a.mode == GM_IBM1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Fi[c] = fint[c * M + i];
     }
-  } else if (a.mode == GM_IBM_HALF || a.mode == GM_IBM1) {
+    const double* P = at_aux ? a.aux : a.pos;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) Fi[c] = fint[c * M + i];
+    for (int c = 0; c < 3; ++c) X[c] = P[c * M + i];
   }
   const int home = a.keys ? (int)a.keys[k] : 0;
 
-  const bool at_aux = a.mode == GM_IBM_HALF || a.mode == GM_IBM_FINAL;
-  const double* P = at_aux ? a.aux : a.pos;
   int b[3];
   C w[3][4];
-  double X[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    X[c] = P[c * M + i];
-    stencil_1d<ST, C>(X[c], b[c], w[c]);
-  }
+  for (int c = 0; c < 3; ++c) stencil_1d<ST, C>(X[c], b[c], w[c]);
 
   C own[3] = {C(0), C(0), C(0)};
   if (a.mode != GM_IBM1) {
@@ -843,16 +868,15 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
               }
             }
       if (a.keys) {
-        // the bins of this step are valid while the marker stays within one
-        // cell of its home tile
+        // the bins are valid while every stencil node lies within three
+        // cells of the home tile (the reach of the spreading's neighbour
+        // search)
         const int t = home;
         const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
         bool ok = true;
         for (int c = 0; c < 3; ++c) {
-          int cell = (int)floor(X[c]);
-          if (!per[c]) cell = cell < 0 ? 0 : (cell >= n3[c] ? n3[c] - 1 : cell);
           const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
-          ok = ok && near_home(cell, lo, hi, n3[c], per[c]);
+          ok = ok && stencil_near_home<SN>(b[c], lo, hi, n3[c], per[c]);
         }
         if (!ok) *a.status = 1;
       }
