@@ -168,6 +168,7 @@ def run_gpu(args, rank, world, local_rank):
         box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
         box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
                           bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+        shape = box.autotune()           # LB launch shape, before any timing
         box.step(args.warmup)
         box.set_option(lbc.LBC_OPT_TIMING, steps + 4)
         # the graphs are recaptured with timing nodes: one eager step + one
@@ -175,7 +176,7 @@ def run_gpu(args, rank, world, local_rank):
         box.step(3)
         box.lb_timing(reset=True)
         r = {"launches_per_step": box.launches_per_step(),
-             "pop_bytes": box.population_bytes()}
+             "pop_bytes": box.population_bytes(), "lb_block": list(shape)}
         clocks = ClockSampler(local_rank) if sample_clocks else None
         if clocks:
             clocks.start()
@@ -235,7 +236,7 @@ def run_gpu(args, rank, world, local_rank):
                            "ms_per_step": r["ms_max"] / nform,
                            "lb_avg_ms": r["lb_avg_ms"], "lb_achieved_gbs": r["achieved"],
                            "lb_frac_of_peak": r["achieved"] / peak,
-                           "alg_bytes_per_cell": BYTES_PER_CELL[st16]}
+                           "alg_bytes_per_cell": BYTES_PER_CELL[st16], "lb_block": r["lb_block"]}
 
     # end to end through the C ABI with host buffers: upload particles,
     # step, read particles and invariants back (copies inside the timing)
@@ -280,7 +281,8 @@ def run_gpu(args, rank, world, local_rank):
                    "stencil": "trilinear", "split": "Eq. multistep, n=4 coupled sub-steps per half",
                    "body_force": list(c["body_force"]),
                    "l2": "inputs larger than L2 (2 x %.2f GB population arrays)" % (pop_bytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "lb_block": main["lb_block"]},
         "roofline": {"bound": "hbm", "kernel": "lb_step_kernel (fused LB step)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

@@ -250,6 +250,17 @@ lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
 lbc_status lbc_box_lb_timing(lbc_box* box, double* ms_total, int64_t* launches,
                              int32_t reset);
 
+/* Pick the launch shape of the box's fused LB step by timing the candidate
+ * block shapes (rows of 256, 128 or 64 cells; 2-8 rows of 32-128 cells) on
+ * the box's own arrays (only the spare population array is written, the
+ * state is unchanged) and keep the fastest; identical boxes (size, storage,
+ * collision variant, walls, forcing) reuse the first result in the process.
+ * The shape does not change results (one cell per thread either way).
+ * Writes the chosen shape to block_x, block_y (may be NULL).  Synchronises
+ * the stream.  LBC_ERR_STATE for batch members.  No counterpart in the
+ * paper. */
+lbc_status lbc_box_autotune(lbc_box* box, void* stream, int32_t* block_x, int32_t* block_y);
+
 /* Number of kernel launches one time step enqueues for this box (for
  * launch accounting). */
 int64_t lbc_box_launches_per_step(const lbc_box* box);

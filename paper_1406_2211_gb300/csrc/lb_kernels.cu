@@ -300,12 +300,15 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
   }
 }
 
+// block = bx x by cells of one z plane (bx * by <= 256; the shape is the
+// tuning parameter, see lbc_box_autotune)
 template <typename S, int COLL, bool WALLS, bool FORCED, typename IX>
 __global__ void __launch_bounds__(256, 5)
 lb_step_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= a.g.nx) return;
-  lb_cell<S, COLL, WALLS, FORCED, IX>(fin, fout, a, x, blockIdx.y, blockIdx.z);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= a.g.nx || y >= a.g.ny) return;
+  lb_cell<S, COLL, WALLS, FORCED, IX>(fin, fout, a, x, y, blockIdx.z);
 }
 
 // Many boxes in one launch: block b advances one x-row of the box whose row
@@ -340,10 +343,23 @@ static dim3 cell_grid(const Geom& g, int* bx) {
   return dim3((g.nx + b - 1) / b, g.ny, g.nz);
 }
 
+// launch shape of the LB step: the tuned one if set, else rows of up to
+// 256 cells
+static void lb_shape(const LBArgs& a, dim3* grid, dim3* block) {
+  int bx = a.block_x, by = a.block_y;
+  if (bx <= 0 || by <= 0 || bx * by > 256) {
+    bx = ((a.g.nx + 31) / 32) * 32;
+    if (bx > 256) bx = 256;
+    by = 1;
+  }
+  *block = dim3(bx, by, 1);
+  *grid = dim3((a.g.nx + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
+}
+
 template <typename S>
 static void lb_dispatch(const void* fin, void* fout, const LBArgs& a, cudaStream_t s) {
-  int bx;
-  dim3 grid = cell_grid(a.g, &bx);
+  dim3 grid, bx;
+  lb_shape(a, &grid, &bx);
   const bool forced = a.Fa != nullptr || a.Fb != nullptr;
   const S* in = static_cast<const S*>(fin);
   S* out = static_cast<S*>(fout);

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1280,6 +1282,83 @@ int64_t lbc_box_launches_per_step(const lbc_box* b) {
 size_t lbc_box_population_bytes(const lbc_box* b) { return b ? b->L.pop_bytes : 0; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ autotuning
+namespace {
+struct TuneKey {
+  int nx, ny, nz, storage, coll, walls, forced;
+  bool operator<(const TuneKey& o) const {
+    const int a[7] = {nx, ny, nz, storage, coll, walls, forced};
+    const int c[7] = {o.nx, o.ny, o.nz, o.storage, o.coll, o.walls, o.forced};
+    for (int k = 0; k < 7; ++k)
+      if (a[k] != c[k]) return a[k] < c[k];
+    return false;
+  }
+};
+std::mutex g_tune_lock;
+std::map<TuneKey, std::pair<int, int>> g_tuned;   // shape of every key tuned so far
+}  // namespace
+
+extern "C" lbc_status lbc_box_autotune(lbc_box* b, void* stream, int32_t* block_x,
+                                       int32_t* block_y) {
+  if (!b) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;
+  cudaStream_t s = S(stream);
+  // the LB step as the box runs it: forced when it has particles
+  LBArgs a = b->lb;
+  if (b->L.has_particles) {
+    a.Fa = b->F(b->ia); a.flag_a = b->flag(b->ia);
+    a.Fb = b->F(1 - b->ia); a.flag_b = b->flag(1 - b->ia);
+    a.ca = make_real(0.5); a.cb = make_real(0.5);
+  }
+  const Geom& g = b->L.g;
+  const TuneKey key{g.nx, g.ny, g.nz, b->lat.storage, lb_collision_variant(a), g.walls,
+                    b->L.has_particles ? 1 : 0};
+  std::pair<int, int> best{0, 0};
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> guard(g_tune_lock);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) { best = it->second; cached = true; }
+  }
+  if (!cached) {
+    // candidate shapes (threads <= 256): rows, and tiles of a few rows that
+    // share the y-neighbour pulls in L1
+    const int shapes[8][2] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}, {64, 4}, {32, 4}, {32, 8}, {64, 1}};
+    const int rx = ((g.nx + 31) / 32) * 32;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 0.0f;
+    // the LB step writes the spare population array only: state unchanged
+    void* out = b->pop(1 - b->cur);
+    for (const auto& sh : shapes) {
+      if (sh[0] > rx || sh[1] > g.ny) continue;
+      a.block_x = sh[0];
+      a.block_y = sh[1];
+      launch_lb_step(b->lat.storage, b->pop(b->cur), out, a, s);     // warm-up
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_lb_step(b->lat.storage, b->pop(b->cur), out, a, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (best.first == 0 || ms < best_ms) { best_ms = ms; best = {sh[0], sh[1]}; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbc_status st = last_launch();
+    if (st != LBC_OK) return st;
+    std::lock_guard<std::mutex> guard(g_tune_lock);
+    g_tuned[key] = best;
+  }
+  b->lb.block_x = best.first;
+  b->lb.block_y = best.second;
+  reset_graphs(b);                  // captured steps hold the old shape
+  if (block_x) *block_x = best.first;
+  if (block_y) *block_y = best.second;
+  return LBC_OK;
+}
 
 // ------------------------------------------------------------ batching
 // Members advance together: per batched step, the phase-1 part of every

@@ -28,6 +28,7 @@ struct LBArgs {
   // FP64 storage, float otherwise), one activity flag per force tile
   const void* Fa; const uint8_t* flag_a;
   const void* Fb; const uint8_t* flag_b;
+  int block_x, block_y;   // LB launch shape (0: default rows of up to 256 cells)
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
   float rscale16;         // 1 / scale16
 };

@@ -89,6 +89,7 @@ _PROTOS = {
     "lbc_box_get_fields": (_S, [_P, _P, _P, _P]),
     "lbc_box_get_particles": (_S, [_P, _P, _P, _P, _P]),
     "lbc_box_get_stress": (_S, [_P, _P, _P]),
+    "lbc_box_autotune": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbc_box_invariants": (_S, [_P, _P, _P, _P]),
     "lbc_box_status": (_S, [_P]),
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
@@ -320,6 +321,13 @@ class Box:
         check(self.lib.lbc_box_get_fields(self.handle, _ptr(rho), _ptr(u), self._s()),
               "lbc_box_get_fields")
         return rho, u
+
+    def autotune(self):
+        """Tune the LB launch shape (lbc_box_autotune); returns (bx, by)."""
+        bx, by = C.c_int32(), C.c_int32()
+        check(self.lib.lbc_box_autotune(self.handle, self._s(), C.byref(bx), C.byref(by)),
+              "lbc_box_autotune")
+        return int(bx.value), int(by.value)
 
     def get_stress(self):
         """Viscous stress sigma[6][nz][ny][nx] (xx, yy, zz, xy, yz, xz)."""

@@ -130,3 +130,22 @@ def test_graphs_and_eager_launches_agree_bitwise():
     assert np.array_equal(a.get_populations(), b.get_populations())
     a.close()
     b.close()
+
+
+def test_autotuned_launch_shape_keeps_results():
+    """lbc_box_autotune picks a block shape by timing; the shape changes no
+    result (one cell per thread) and identical boxes reuse it."""
+    require_cuda()
+    shape = (12, 20, 40)
+    fbar0 = synth.random_populations(shape, seed=31, amp=1e-3)
+    ref, _ = make_pair(shape, fbar0, coll="mrt", tau=0.9, storage="f32", g=(1e-5, 0, 0))
+    box, _ = make_pair(shape, fbar0, coll="mrt", tau=0.9, storage="f32", g=(1e-5, 0, 0))
+    bx, by = box.autotune()
+    assert (bx, by) in {(256, 1), (128, 1), (128, 2), (64, 2), (64, 4), (32, 4), (32, 8), (64, 1)}
+    assert bx * by <= 256 and by <= shape[1]
+    assert np.array_equal(box.get_populations(), ref.get_populations())   # state unchanged
+    box.step(7)
+    ref.step(7)
+    assert np.array_equal(box.get_populations(), ref.get_populations())
+    other, _ = make_pair(shape, fbar0, coll="mrt", tau=0.9, storage="f32", g=(1e-5, 0, 0))
+    assert other.autotune() == (bx, by)
