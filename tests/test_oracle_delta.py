@@ -109,3 +109,32 @@ def test_tiny_periodic_box_folds_the_stencil():
     for kind in ("trilinear", "peskin3", "peskin4"):
         g = delta.spread(np.array([[1.0, 2.0, 3.0]]), pos, shape, kind)
         assert np.allclose(g[:, 0, 0, 0], [1.0, 2.0, 3.0], atol=1e-15)
+
+
+def _golden_phi3():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "phi3_printed_values.txt")
+    pts, C = [], None
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] == "C":
+            C = int(line[1]) / int(line[2])
+        else:
+            rn, rd, pn, pd = (int(v) for v in line)
+            pts.append((rn / rd, pn / pd))
+    return pts, C
+
+
+def test_phi3_matches_printed_values():
+    """phi_3 at the points where the appendix's printed closed form is
+    rational (tests/golden/phi3_printed_values.txt), and its Eq. [delta3]
+    constant from those values."""
+    from oracle import delta as OD
+    pts, C = _golden_phi3()
+    r = np.array([p[0] for p in pts])
+    assert np.allclose(OD.phi_peskin3(r), [p[1] for p in pts], rtol=0, atol=1e-15)
+    for x in np.linspace(-0.5, 0.5, 11):
+        j = np.arange(-3, 4)
+        assert abs((OD.phi_peskin3(x - j) ** 2).sum() - C) < 1e-15
