@@ -1051,7 +1051,6 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   constexpr int SN = nodes_1d<ST>();
   constexpr int WARPS = SPREAD_THREADS / 32;
   __shared__ SpreadHit<C> shit[WARPS][32];
-  __shared__ int s_nlive;
   const Geom& g = p.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   SpreadHit<C>* stage = shit[wid];
@@ -1059,21 +1058,31 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   C* F = static_cast<C*>(a.F);
   const int ntiles = g.ntx * g.nty * g.ntz;
   const bool perz = !g.walls;
-  if (threadIdx.x == 0) s_nlive = *a.nlive;
   // tiles no stencil reaches keep their flag when accumulating and are
-  // cleared otherwise; the marks are consumed
+  // cleared otherwise; the marks are consumed (the live tiles are other
+  // tiles, so the warps go on without waiting for each other)
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
        t += (long long)gridDim.x * blockDim.x) {
     if (a.mark[t] != 0u) a.mark[t] = 0u;
     else if (!a.accumulate) a.flag[t] = 0;
   }
-  __syncthreads();
-  const int nlive = s_nlive;
+  const int nlive = __shfl_sync(0xffffffffu, lane == 0 ? *a.nlive : 0, 0);
   const int cxl = lane & 3, cyl = (lane >> 2) & 3, czl = lane >> 4;
   // axes on which a stencil meets a tile only by shifting (see tile_offset)
   const bool shx = g.nx >= 2 * TILE, shy = g.ny >= 2 * TILE, shz = !perz || g.nz >= 2 * TILE;
-  for (int j = blockIdx.x * WARPS + wid; j < nlive; j += gridDim.x * WARPS) {
-    const int4 lt = a.live_tiles[j];
+  // axes of whole tiles: the neighbour tiles are t - 1, t, t + 1 (wrapped, or
+  // clipped at walls), the same list the table holds
+  const int n3[3] = {g.nx, g.ny, g.nz}, ntv[3] = {g.ntx, g.nty, g.ntz};
+  bool whole[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    whole[d] = n3[d] % TILE == 0 && (!(d < 2 || perz) || ntv[d] >= 3);
+  const int stride = gridDim.x * WARPS;
+  int j = blockIdx.x * WARPS + wid;
+  int4 lt_next = j < nlive ? a.live_tiles[j] : make_int4(0, 0, 0, 0);
+  for (; j < nlive; j += stride) {
+    const int4 lt = lt_next;
+    if (j + stride < nlive) lt_next = a.live_tiles[j + stride];   // next tile, ahead of use
     const int t = lt.x;
     const int tt[3] = {lt.y, lt.z, lt.w};
     const int lo[3] = {tt[0] * TILE, tt[1] * TILE, tt[2] * TILE};
@@ -1088,13 +1097,25 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
       if (in0) load_force(F, cell0, acc0[0], acc0[1], acc0[2]);
       if (in1) load_force(F, cell1, acc1[0], acc1[1], acc1[2]);
     }
-    // neighbour tiles per axis: lane q < 8 reads entry q of each table row
+    // neighbour tiles per axis: lane q holds entry q of the list (from the
+    // table on axes of partial or few tiles)
     int rowv[3], nt[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int* row = a.ntab + (d * a.maxnt + tt[d]) * MAXNT;
-      rowv[d] = lane < MAXNT ? row[lane] : -1;
-      nt[d] = __popc(__ballot_sync(0xffffffffu, rowv[d] >= 0));
+      if (whole[d]) {
+        const bool periodic = d < 2 || perz;
+        const int first = periodic ? tt[d] - 1 : max(tt[d] - 1, 0);
+        const int last = periodic ? tt[d] + 1 : min(tt[d] + 1, ntv[d] - 1);
+        nt[d] = last - first + 1;
+        int v = first + lane;
+        if (v < 0) v += ntv[d];
+        else if (v >= ntv[d]) v -= ntv[d];
+        rowv[d] = lane < nt[d] ? v : -1;
+      } else {
+        const int* row = a.ntab + (d * a.maxnt + tt[d]) * MAXNT;
+        rowv[d] = lane < MAXNT ? row[lane] : -1;
+        nt[d] = __popc(__ballot_sync(0xffffffffu, rowv[d] >= 0));
+      }
     }
     const int ncand = nt[0] * nt[1] * nt[2];
     // candidate markers: the ranges of the neighbour tiles, flattened; 32
