@@ -95,7 +95,9 @@ __device__ inline void store_force(double* F, IX cell, double x, double y, doubl
 // Random bits for the stochastic rounding of the values of one cell: a seed
 // from the cell index and one of the cell's own values (so the draws change
 // from step to step, and the same inputs give the same bits), then a short
-// integer mix per population.  Unused (and compiled away) for FP32 / FP64.
+// integer mix per draw (the stores use the low 13 or 16 bits; a draw can
+// serve two values through its two halves).  Unused (and compiled away) for
+// FP32 / FP64.
 struct CellDither {
   uint32_t s;
   __device__ CellDither(long long cell, float salt) {

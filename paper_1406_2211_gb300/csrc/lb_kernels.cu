@@ -203,7 +203,11 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
 
   const C uu0 = div_by<C, 24>(u0x * u0x + u0y * u0y + u0z * u0z);
   const C uu1 = div_by<C, 24>(u1x * u1x + u1y * u1y + u1z * u1z);
-  auto put = [&](int i, C v) { Store<S>::store(fout, static_cast<IX>(i) * qs + cell, v, i, a.rscale16, dz(i)); };
+  // r: random bits of the stochastic rounding (16-bit storage); a pair of
+  // opposite populations shares one 32-bit draw (low and high half)
+  auto put = [&](int i, C v, uint32_t r) {
+    Store<S>::store(fout, static_cast<IX>(i) * qs + cell, v, i, a.rscale16, r);
+  };
 
   if (COLL == 0) {
     // f*_i = gamma fbar_i + n_i [ (1-gamma) rd/36 + c_i.((1-gamma) j + F)/12
@@ -216,7 +220,7 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
     {
       const C q0 = quad_part<C, 0>(u0x, u0y, u0z, uu0);
       const C q1 = quad_part<C, 0>(u1x, u1y, u1z, uu1);
-      put(0, gam * f[0] + C(n_of(0)) * (sm + rho * (q1 - gam * q0)));
+      put(0, gam * f[0] + C(n_of(0)) * (sm + rho * (q1 - gam * q0)), dz(0));
     }
     unroll_pairs([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -224,8 +228,9 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
       const C q1 = quad_part<C, i>(u1x, u1y, u1z, uu1);
       const C E = C(n_of(i)) * (sm + rho * (q1 - gam * q0));
       const C O = C(n_of(i)) * lin_part<C, i>(qx, qy, qz);
-      put(i, gam * f[i] + (E + O));
-      put(i + 1, gam * f[i + 1] + (E - O));
+      const uint32_t r = dz(i);
+      put(i, gam * f[i] + (E + O), r);
+      put(i + 1, gam * f[i + 1] + (E - O), r >> 16);
     });
   } else if (COLL == 2) {
     // MRT with both ghost groups fully relaxed (their eigenvalue 1 - lambda
@@ -264,13 +269,14 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
       if constexpr (mrt_e(9, i) != 0) post += C(mrt_e(9, i)) * m[9];
       return C(n_of(i)) * (md + rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + C(w_of(i)) * post;
     };
-    put(0, even(IC<0>{}));
+    put(0, even(IC<0>{}), dz(0));
     unroll_pairs([&](auto I) {
       constexpr int i = decltype(I)::value;
       const C E = even(I);
       const C O = C(n_of(i)) * lin_part<C, i>(j1x, j1y, j1z);
-      put(i, E + O);
-      put(i + 1, E - O);
+      const uint32_t r = dz(i);
+      put(i, E + O, r);
+      put(i + 1, E - O, r >> 16);
     });
   } else {
     // neq_i = fbar_i - f_i^eq(rho, u0); relax per moment; add f^eq(rho, u1)
@@ -294,7 +300,7 @@ __device__ __forceinline__ void lb_cell(const S* __restrict__ fin, S* __restrict
       constexpr int i = decltype(I)::value;
       const C v = C(n_of(i)) * (md + lin_part<C, i>(j1x, j1y, j1z) +
                                 rho * quad_part<C, i>(u1x, u1y, u1z, uu1)) + post[i];
-      put(i, v);
+      put(i, v, dz(i));
     };
     unroll_q(out);
   }
