@@ -124,3 +124,27 @@ def test_product_package_does_not_use_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\b(import|from)\s+oracle\b", text), f
                 assert "oracle/" not in text, f
+
+
+def test_batch_bytes_required_host_only(lib):
+    n1 = lib.lbc_batch_bytes_required(1)
+    n8 = lib.lbc_batch_bytes_required(8)
+    assert n1 > 0 and n8 == 8 * n1                 # tables scale with the slots
+    assert lib.lbc_batch_bytes_required(0) == 0
+    assert lib.lbc_batch_bytes_required(2000) == 0  # above the 1024-slot limit
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_1406_2211_gb300 import lbc
+    out = C.c_void_p()
+    fin = (C.c_void_p * 1)()
+    nfin, done, n = C.c_int32(), C.c_int64(), C.c_int64()
+    assert lib.lbc_batch_create(0, None, 0, C.byref(out)) == lbc.LBC_ERR_ARG
+    assert lib.lbc_batch_add(None, None, 1) == lbc.LBC_ERR_ARG
+    assert lib.lbc_batch_remove(None, None) == lbc.LBC_ERR_ARG
+    assert lib.lbc_batch_remaining(None, None, C.byref(n)) == lbc.LBC_ERR_ARG
+    assert lib.lbc_batch_advance(None, 1, None, fin, C.byref(nfin), C.byref(done)) == lbc.LBC_ERR_ARG
+    assert lib.lbc_batch_size(None) == -1
+    assert lib.lbc_batch_destroy(None) == lbc.LBC_ERR_ARG
+    assert lib.lbc_box_get_stress(None, None, None) == lbc.LBC_ERR_ARG
+    assert lib.lbc_box_autotune(None, None, None, None) == lbc.LBC_ERR_ARG
