@@ -298,6 +298,84 @@ def run_gpu(args, rank, world, local_rank):
     return line
 
 
+# ------------------------------------------------------------------ other workloads
+def other_workload_boxes(name, storage):
+    """Full-size box of the shell (IBM) or rigid-sphere (modified EBF)
+    workload with its particles set."""
+    import numpy as np
+    import synth
+    from paper_1406_2211_gb300 import lbc
+    c = synth.config(name)
+    nx, ny, nz = c["box"]
+    if name.startswith("cfg3"):
+        pos, edges, r0 = synth.shells(c["nshells"], c["radius"], c["box"], c["seed"],
+                                      c["subdivisions"])
+        lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"],
+                               walls=True, wall_velocity=c["wall_velocity"], storage=storage)
+        cpl = lbc.coupling_desc("ibm", 2, c["stencil"])
+        box = lbc.Box(lat, cpl, max_particles=len(pos), max_bonds=len(edges))
+        box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+        box.set_particles(pos, bonds=edges, bond_k=c["spring_k"], bond_r0=r0)
+        desc = "%d shells x 642 IBM markers, springs k = %g, walls -/+%g, Peskin-4" % (
+            c["nshells"], c["spring_k"], c["wall_velocity"][1][0])
+    else:
+        pos, first, count = synth.rigid_spheres(c["nspheres"], c["radius"], c["markers"],
+                                                c["box"], seed=c["seed"])
+        mass = c["rho0"] * 4.0 / 3.0 * np.pi * c["radius"] ** 3 / c["markers"]
+        lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"], storage=storage)
+        cpl = lbc.coupling_desc("mebf", 2, c["stencil"])
+        box = lbc.Box(lat, cpl, max_particles=len(pos))
+        box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+        rng = np.random.default_rng(c["seed"])
+        box.set_particles(pos, vel=0.002 * rng.standard_normal(pos.shape), mass=mass,
+                          rigid=dict(first=first, count=count, radius=c["radius"],
+                                     k=c["rigid_k"], repulsion_k=c["repulsion_k"]))
+        desc = "%d rigid spheres x %d markers (tethers k = %g), modified EBF, Peskin-4, tau = %g" % (
+            c["nspheres"], c["markers"], c["rigid_k"], c["tau"])
+    return box, nx * ny * nz, desc
+
+
+def run_other_workloads(args, peak):
+    """The shell and rigid-sphere workloads at full size: coupled MLUPS over
+    `steps` steps (CUDA events) and the LB kernel's fraction of the peak."""
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    out = {}
+    steps = min(args.steps, 60)
+    for name, storages in (("cfg3_ibm_shells_192", ("f32", "bf16dev")),
+                           ("cfg4_mebf_spheres_128", ("f32",))):
+        out[name] = {}
+        for st in storages:
+            box, cells, desc = other_workload_boxes(name, st)
+            shape = box.autotune()
+            box.step(args.warmup)
+            box.set_option(lbc.LBC_OPT_TIMING, steps + 4)
+            box.step(3)
+            box.lb_timing(reset=True)
+            stream = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            box.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            lb_ms, lb_n = box.lb_timing(reset=True)
+            _, _, status = box.invariants()
+            box.close()
+            del box
+            torch.cuda.empty_cache()
+            if status != 0:
+                raise RuntimeError("non-finite state in %s (%s)" % (name, st))
+            lb_avg = lb_ms / lb_n
+            out[name][st] = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                             "steps": steps, "ms_per_step": ms / steps, "lb_avg_ms": lb_avg,
+                             "lb_frac_of_peak": BYTES_PER_CELL[st] * cells / (lb_avg * 1e-3) / 1e9 / peak,
+                             "lb_block": list(shape), "model": desc}
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def serving_jobs(njobs, seed, step_scale, rate=None):
     """A bounded sample of the serving ensemble: cubic periodic boxes of edge
@@ -472,6 +550,8 @@ def main():
     line["cpu_baseline"] = cpu
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["other_workloads"] = run_other_workloads(args, line["roofline"]["peak"])
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
