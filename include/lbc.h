@@ -239,10 +239,28 @@ lbc_status lbc_box_status(const lbc_box* box);
  *  LBC_OPT_TIMING  n > 0: bracket each of the next n launches of the fused
  *                  LB kernel with a pair of CUDA events recorded on the
  *                  launching stream (inside the graphs as event-record
- *                  nodes); 0 = off.  Read with lbc_box_lb_timing(). */
+ *                  nodes); 0 = off.  Read with lbc_box_lb_timing().
+ *  LBC_OPT_NODE_MOMENTS  1 = after each LB step of a coupled step, one pass
+ *                  stores j = sum_i fbar_i c_i and 1 / rho (the moments of
+ *                  the interpolated velocity, Eq. [IBM-interpolation]) for
+ *                  every cell in the tiles within one tile of a marker, and
+ *                  the interpolations between two LB steps read them instead
+ *                  of pulling 19 populations per stencil node; 0 = every
+ *                  interpolation pulls.  Results are identical either way.
+ *                  Not available with the multiple-time-step split inside
+ *                  LB (LBC_SPLIT_INSIDE, substeps > 1), which caches the
+ *                  moments per marker instead (LBC_ERR_STATE).  Default:
+ *                  on when M x (stencil nodes) x (interpolations per LB
+ *                  step) >= half the lattice's cells, M = max_particles.
+ * Errors: LBC_ERR_ARG for an unknown option or value, LBC_ERR_STATE for a
+ * batch member.  Setting an option drops the captured step graphs. */
 #define LBC_OPT_GRAPHS 1
 #define LBC_OPT_TIMING 2
+#define LBC_OPT_NODE_MOMENTS 3
 lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
+
+/* Current value of an option (LBC_OPT_TIMING: the event pairs reserved). */
+lbc_status lbc_box_get_option(const lbc_box* box, int32_t option, int64_t* value);
 
 /* Sum of the event-measured durations (ms) of the LB kernel launches timed
  * since the last reset, and their count; waits for the last event.

@@ -67,6 +67,7 @@ struct Layout {
   size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
   size_t off_home, off_sortflags;     // home tile per marker; {need, changed} per step parity
   size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
+  size_t off_mom, off_mready;        // node-moment field and its ready tiles (other schemes)
   // rigid bodies (at most one per marker)
   size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
       off_rb_frep;
@@ -74,6 +75,7 @@ struct Layout {
   int ntiles, maxnt;
   bool has_particles;
   bool use_ncache;
+  bool has_mom;
 };
 
 Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_t M, int64_t B) {
@@ -138,6 +140,11 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_ncache = take(multistep ? (size_t)sn * sn * sn * 4 * M * force_elem_bytes(l->storage) : 0);
     L.off_ncache_b = take(multistep ? (size_t)M * 16 : 0);
     L.use_ncache = multistep;
+    // the other schemes can read the node moments from a field filled once
+    // per LB step
+    L.has_mom = !multistep;
+    L.off_mom = take(L.has_mom ? fbytes : 0);
+    L.off_mready = take(L.has_mom ? (size_t)L.ntiles : 0);
     L.off_rb_first = take((size_t)M * 4);
     L.off_rb_count = take((size_t)M * 4);
     L.off_rb_radius = take((size_t)M * 8);
@@ -186,6 +193,7 @@ struct lbc_box {
   int64_t nrigid;      // rigid bodies set by lbc_box_set_particles
   double rigid_k, rigid_krep;
   lbc_batch* batch;    // the batch this box belongs to, or null
+  bool mom_on;         // gathers read the node-moment field (LBC_OPT_NODE_MOMENTS)
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
   void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
@@ -248,6 +256,16 @@ void fill_lb_args(lbc_box* b) {
 bool order2(const lbc_box* b) { return b->cpl.order == 2; }
 bool particles(const lbc_box* b) { return b->L.has_particles && b->M > 0; }
 
+// the node-moment pass (one pull of every cell in the tiles near markers)
+// pays when the gathers between two LB steps would otherwise pull at least
+// half as many stencil nodes as the lattice has cells
+bool moments_pay(const Layout& L, const lbc_coupling_desc& c, int64_t M) {
+  const double sn = c.stencil == LBC_TRILINEAR ? 2.0 : (c.stencil == LBC_PESKIN4 ? 4.0 : 3.0);
+  const double gathers = c.kind == LBC_IBM ? (c.order == 2 ? 3.0 : 2.0) : (c.order == 2 ? 2.0 : 1.0);
+  const double cells = (double)L.g.nx * L.g.ny * L.g.nz;
+  return (double)M * sn * sn * sn * gathers >= 0.5 * cells;
+}
+
 PartArgs part_args(lbc_box* b) {
   PartArgs p;
   p.g = b->L.g;
@@ -268,7 +286,17 @@ struct Plan {
   int phase = 0;
   bool after_lb = false;
   int par = 0;     // step parity (the population buffer at the start of the step)
+  bool mom_after = false;   // refill the node-moment field after the LB step
   bool on() const { return phase == 0 || (phase == 1) != after_lb; }
+
+  void moments() {
+    if (!mom_after) return;
+    GatherArgs a = gather_base();
+    launch_node_moments(part_args(b), a, b->binned ? b->iptr(b->L.off_tb) : nullptr,
+                        b->iptr(b->L.off_te), b->arena + b->L.off_mom,
+                        reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready), s);
+    ++n;
+  }
 
   void lb(const void* Fa, const void* Fb, double ca, double cb, double cg) {
     LBArgs a = b->lb;
@@ -285,6 +313,7 @@ struct Plan {
         b->cur = 1 - b->cur;
       }
       after_lb = true;
+      if (phase == 2) moments();
       return;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -306,6 +335,7 @@ struct Plan {
     if (e1) cudaEventRecordWithFlags(e1, s, rf);
     b->cur = 1 - b->cur;
     ++n;
+    moments();
   }
 
   // drift / intrinsic forces / kick / drift; input the current particle
@@ -413,6 +443,10 @@ struct Plan {
     a.nlive = b->iptr(b->L.off_nlive);
     a.ncache = b->arena + b->L.off_ncache;
     a.ncache_b = reinterpret_cast<int4*>(b->arena + b->L.off_ncache_b);
+    if (b->mom_on) {
+      a.mom = b->arena + b->L.off_mom;
+      a.mready = reinterpret_cast<const uint8_t*>(b->arena + b->L.off_mready);
+    }
     return a;
   }
 
@@ -471,6 +505,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     *launches += P.n;
     return;
   }
+  P.mom_after = b->mom_on;
   const int ia = b->ia, ib = 1 - b->ia;
   if (kind == LBC_IBM) {
     if (order2(b)) {
@@ -723,6 +758,13 @@ void free_timing(lbc_box* b) {
   b->timing_used = 0;
 }
 
+// no tile of the node-moment field is ready (until the next LB step refills
+// it)
+void moments_stale(lbc_box* b, cudaStream_t s) {
+  if (b->L.has_particles && b->L.has_mom)
+    cudaMemsetAsync(b->arena + b->L.off_mready, 0, (size_t)b->L.ntiles, s);
+}
+
 // the populations were replaced from outside a step: node moments cached
 // for the next step's first half are stale
 void populations_changed(lbc_box* b, cudaStream_t s) {
@@ -730,6 +772,7 @@ void populations_changed(lbc_box* b, cudaStream_t s) {
   int* f = b->iptr(b->L.off_sortflags);
   cudaMemsetAsync(f + 1, 1, sizeof(int), s);
   cudaMemsetAsync(f + 3, 1, sizeof(int), s);
+  moments_stale(b, s);
 }
 
 lbc_status clear_pending(lbc_box* b, cudaStream_t s) {
@@ -876,6 +919,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->batch = nullptr;
   b->nrigid = 0;
   b->rigid_k = b->rigid_krep = 0.0;
+  b->mom_on = L.has_particles && L.has_mom && moments_pay(L, b->cpl, max_particles);
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -886,7 +930,8 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
         cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b->arena + L.off_mark, 0, (size_t)L.ntiles * 4) != cudaSuccess ||
         cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess ||
-        cudaMemset(b->arena + L.off_sortflags, 0, 4 * sizeof(int)) != cudaSuccess) {
+        cudaMemset(b->arena + L.off_sortflags, 0, 4 * sizeof(int)) != cudaSuccess ||
+        (L.has_mom && cudaMemset(b->arena + L.off_mready, 0, (size_t)L.ntiles) != cudaSuccess)) {
       delete b;
       return LBC_ERR_CUDA;
     }
@@ -1016,6 +1061,7 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
   if (p->nbonds > 0 && (!p->bond_ij || !p->bond_k || !p->bond_r0)) return LBC_ERR_ARG;
   if (!b->L.has_particles) return p->n == 0 ? LBC_OK : LBC_ERR_STATE;
   cudaStream_t s = S(stream);
+  moments_stale(b, s);     // steps without particles did not refill the field
   const int64_t M = p->n;
   const int64_t Mx = b->maxM;
   const Geom& g = b->L.g;
@@ -1253,7 +1299,30 @@ lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
     b->timing_cap = value;
     return LBC_OK;
   }
+  if (option == LBC_OPT_NODE_MOMENTS) {
+    if (value != 0 && value != 1) return LBC_ERR_ARG;
+    if (value == 1 && !(b->L.has_particles && b->L.has_mom)) return LBC_ERR_STATE;
+    if (b->mom_on == (value == 1)) return LBC_OK;
+    reset_graphs(b);
+    b->mom_on = value == 1;
+    // steps taken while it was off left the field behind the populations
+    if (b->mom_on) {
+      CK(cudaDeviceSynchronize());
+      CK(cudaMemset(b->arena + b->L.off_mready, 0, (size_t)b->L.ntiles));
+      CK(cudaDeviceSynchronize());
+    }
+    return LBC_OK;
+  }
   return LBC_ERR_ARG;
+}
+
+lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) {
+  if (!b || !value) return LBC_ERR_ARG;
+  if (option == LBC_OPT_GRAPHS) *value = b->use_graphs;
+  else if (option == LBC_OPT_TIMING) *value = b->timing_cap;
+  else if (option == LBC_OPT_NODE_MOMENTS) *value = b->mom_on ? 1 : 0;
+  else return LBC_ERR_ARG;
+  return LBC_OK;
 }
 
 lbc_status lbc_box_lb_timing(lbc_box* b, double* ms_total, int64_t* launches, int32_t reset) {

@@ -189,6 +189,11 @@ struct GatherArgs {
   // [node][slot] of 4 values; ncache_b[k] holds the base it was taken at.
   int cache; void* ncache; int4* ncache_b;
   const int* invalidate;          // reuse only while *invalidate == 0 (null: no check)
+  // node-moment field: j and 1 / rho of every cell as a 4-vector in the
+  // compute type (force-field layout), valid in the tiles with
+  // mready[tile] != 0 (the others are pulled from the populations); null:
+  // unused.  The same function computes both, so the two agree bit for bit.
+  const void* mom; const uint8_t* mready;
   // fused: the thread of slot k first runs the drift sub-step `drift` of
   // its marker (mode GM_COUPLE; positions, velocities and F_int come from it)
   int fused;
@@ -209,6 +214,11 @@ struct GatherArgs {
   int* nlive;
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
+// fills the node-moment field from a.pops in every tile within one tile of
+// a tile that holds a marker (tb / te: the bins; null: every tile), sets
+// ready[tile] to 1 there and to 0 elsewhere
+void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
+                         void* mom, uint8_t* ready, cudaStream_t s);
 
 struct SpreadArgs {
   const void* rec;                            // StencilRecT<C>[M]

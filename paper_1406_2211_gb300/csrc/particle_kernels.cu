@@ -350,38 +350,72 @@ rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
   }
 }
 
-// one thread per body: repulsion from every other body closer than one
-// lattice unit (surface gap), summed in body order
-__global__ void rigid_repulsion_kernel(const PartArgs p, const RigidArgs rg) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= rg.nbodies) return;
+// one warp per body: the lanes take the other bodies in strides of 32; a
+// float screen drops pairs whose centres are farther apart than the reach
+// r_b + r_c + 1 by more than the float rounding of the centres can explain,
+// and the remaining pairs are evaluated in double.  The lane sums are
+// combined by a fixed butterfly, so the result does not depend on
+// scheduling.
+constexpr int REPULSION_THREADS = 128;
+
+__device__ inline float min_image_f(float d, int n, bool periodic) {
+  if (!periodic) return d;
+  const float h = 0.5f * n;
+  if (d > h) d -= n;
+  else if (d < -h) d += n;
+  return d;
+}
+
+__global__ void __launch_bounds__(REPULSION_THREADS)
+rigid_repulsion_kernel(const PartArgs p, const RigidArgs rg) {
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= rg.nbodies) return;                   // whole warps leave together
   const Geom& g = p.g;
   const int n3[3] = {g.nx, g.ny, g.nz};
   const bool per[3] = {true, true, !g.walls};
   const double* Xb = rg.frames + 12 * b;
+  const float xb[3] = {(float)Xb[0], (float)Xb[1], (float)Xb[2]};
+  const double rb = rg.radius[b];
+  // centres lie within a few box extents L of the origin, so rounding them
+  // and their separation to float moves the distance by a few 1e-7 L; the
+  // screen keeps a margin well above that
+  const float slack = 1e-3f + 4e-6f * (float)max(g.nx, max(g.ny, g.nz));
   double Fb[3] = {0.0, 0.0, 0.0};
-  for (int c2 = 0; c2 < rg.nbodies; ++c2) {
+  for (int c2 = lane; c2 < rg.nbodies; c2 += 32) {
     if (c2 == b) continue;
     const double* Xc = rg.frames + 12 * c2;
+    const double rc = rg.radius[c2];
+    const float reach = (float)(rb + rc) + 1.0f + slack;
+    float d2f = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+      const float e = min_image_f((float)Xc[c] - xb[c], n3[c], per[c]);
+      d2f += e * e;
+    }
+    if (d2f > reach * reach) continue;
     double dv[3], d2 = 0.0;
     for (int c = 0; c < 3; ++c) {
       dv[c] = min_image(Xc[c] - Xb[c], n3[c], per[c]);
       d2 += dv[c] * dv[c];
     }
     const double dist = sqrt(d2);
-    const double gap = dist - (rg.radius[b] + rg.radius[c2]);
+    const double gap = dist - (rb + rc);
     if (gap < 1.0 && dist > 0.0) {
       const double mag = rg.krep * (1.0 - gap) / dist;      // pushes b away from c2
       for (int c = 0; c < 3; ++c) Fb[c] -= mag * dv[c];
     }
   }
-  for (int c = 0; c < 3; ++c) rg.frep[3 * b + c] = Fb[c];
+  for (int off = 16; off > 0; off >>= 1)
+    for (int c = 0; c < 3; ++c) Fb[c] += __shfl_xor_sync(0xffffffffu, Fb[c], off);
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) rg.frep[3 * b + c] = Fb[c];
 }
 
 void launch_rigid_frames(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
   if (d.rigid.nbodies <= 0) return;
   rigid_frames_kernel<<<d.rigid.nbodies, FRAME_THREADS, 0, s>>>(p, d);
-  rigid_repulsion_kernel<<<(d.rigid.nbodies + 127) / 128, 128, 0, s>>>(p, d.rigid);
+  const int rb = REPULSION_THREADS / 32;
+  rigid_repulsion_kernel<<<(d.rigid.nbodies + rb - 1) / rb, REPULSION_THREADS, 0, s>>>(p, d.rigid);
 }
 
 void launch_drift(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
@@ -634,7 +668,9 @@ __device__ inline void cache_store(double* p, const double (&j)[3], double inv) 
 
 // fluid velocity at one stencil node (x, y, z) of weight wt, added to own:
 // (((j + c1 F1) + cg g) + c2 F2) / rho, with j and 1 / rho taken from the
-// node cache where it is valid (F1, F2 where their tile flags are set)
+// node cache where it is valid, else from the node-moment field where its
+// tile is ready, else pulled from the populations (F1, F2 where their tile
+// flags are set)
 template <typename S, bool WALLS>
 __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, int x, int y, int z,
                                             typename Store<S>::C wt, bool reuse,
@@ -643,14 +679,17 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
                                             typename Store<S>::C (&own)[3]) {
   using C = typename Store<S>::C;
   C j[3], inv;
+  const long long cell = z * g.plane + (long long)y * g.pitch + x;
+  const int tile = tile_of(g, x, y, z);
   if (reuse) {
     cache_load(slot, j, inv);
   } else {
-    node_base<S, WALLS>(a, g, x, y, z, j, inv);
+    if (a.mom != nullptr && a.mready[tile])
+      cache_load(static_cast<const C*>(a.mom) + 4 * cell, j, inv);
+    else
+      node_base<S, WALLS>(a, g, x, y, z, j, inv);
     if (a.cache != 0) cache_store(slot, j, inv);
   }
-  const long long cell = z * g.plane + (long long)y * g.pitch + x;
-  const int tile = tile_of(g, x, y, z);
   const C* F1 = static_cast<const C*>(a.F1);
   if (F1 && a.flag1[tile]) {
     const C c1 = rv<C>(a.c1);
@@ -669,8 +708,8 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
   own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
 }
 
-// REUSE: launched for sub-steps that read the node cache (fewer registers,
-// more markers in flight); the others keep registers for the population
+// REUSE: launched for sub-steps that read the node cache or the node-moment
+// field (fewer registers, more markers in flight); the others keep registers for the population
 // loads of two nodes at a time
 template <typename S, bool WALLS, int ST, bool REUSE>
 __global__ void __launch_bounds__(GATHER_THREADS, (REUSE && sizeof(typename Store<S>::C) == 4) ? 6 : 4)
@@ -919,7 +958,9 @@ static void gather_str(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
 
 template <typename S, bool WALLS>
 static void gather_st(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
-  if (a.cache == 2) gather_str<S, WALLS, true>(p, a, s);
+  // the lighter variant spills with the wall bounce-back of the pull, which
+  // the field reads still need where a tile is not ready
+  if (a.cache == 2 || (a.mom != nullptr && !WALLS)) gather_str<S, WALLS, true>(p, a, s);
   else gather_str<S, WALLS, false>(p, a, s);
 }
 
@@ -935,6 +976,75 @@ void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
     case ST_F32: gather_s<float>(p, a, s); break;
     case ST_F16: gather_s<__half>(p, a, s); break;
     default: gather_s<__nv_bfloat16>(p, a, s); break;
+  }
+}
+
+// ------------------------------------------------------------ node moments
+// One block per brick of 32 x 4 x 4 cells (eight tiles along x), two cells
+// per thread along z; a warp covers 32 consecutive cells of one row, as in
+// the LB step.  A tile is filled when one of its 27 neighbour tiles (itself
+// included; periodic in x and y, and in z without walls) holds a marker: a
+// marker stays within about a cell of its home tile between re-binnings and
+// its stencil reaches two cells beyond its own, so the gathers find nearly
+// every node in such a tile; a node in a tile that is not ready is pulled
+// from the populations instead.  Without bins every tile is filled.
+constexpr int MOM_THREADS = 256;
+
+template <typename S, bool WALLS>
+__global__ void __launch_bounds__(MOM_THREADS)
+node_moments_kernel(const PartArgs p, const GatherArgs a, const int* __restrict__ tb,
+                    const int* __restrict__ te, void* mom, uint8_t* __restrict__ ready) {
+  using C = typename Store<S>::C;
+  const Geom& g = p.g;
+  __shared__ int need[8];
+  const int t = threadIdx.x;
+  const int tx0 = blockIdx.x * 8, ty = blockIdx.y, tz = blockIdx.z;
+  if (t < 8) need[t] = tb == nullptr ? 1 : 0;
+  __syncthreads();
+  if (tb != nullptr && t < 8 * 27 && tx0 + t / 27 < g.ntx) {
+    const int d = t % 27;
+    const int nx = wrap_int(tx0 + t / 27 + d % 3 - 1, g.ntx);
+    const int ny = wrap_int(ty + (d / 3) % 3 - 1, g.nty);
+    int nz = tz + d / 9 - 1;
+    bool in = true;
+    if (WALLS) in = nz >= 0 && nz < g.ntz;
+    else nz = wrap_int(nz, g.ntz);
+    if (in) {
+      const int n = (nz * g.nty + ny) * g.ntx + nx;
+      if (te[n] > tb[n]) need[t / 27] = 1;
+    }
+  }
+  __syncthreads();
+  if (t < 8 && tx0 + t < g.ntx) ready[(tz * g.nty + ty) * g.ntx + tx0 + t] = (uint8_t)need[t];
+  const int x = blockIdx.x * 32 + (t & 31);
+  const int y = ty * TILE + ((t >> 5) & 3);
+  if (x >= g.nx || y >= g.ny || !need[(t & 31) >> TILE_SHIFT]) return;
+  C* out = static_cast<C*>(mom);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int z = tz * TILE + 2 * (t >> 7) + h;
+    if (z >= g.nz) break;
+    C j[3], inv;
+    node_base<S, WALLS>(a, g, x, y, z, j, inv);
+    cache_store(out + 4 * (z * g.plane + (long long)y * g.pitch + x), j, inv);
+  }
+}
+
+template <typename S>
+static void node_moments_s(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
+                           void* mom, uint8_t* ready, cudaStream_t s) {
+  const dim3 grid((unsigned)((p.g.nx + 31) / 32), (unsigned)p.g.nty, (unsigned)p.g.ntz);
+  if (p.g.walls) node_moments_kernel<S, true><<<grid, MOM_THREADS, 0, s>>>(p, a, tb, te, mom, ready);
+  else node_moments_kernel<S, false><<<grid, MOM_THREADS, 0, s>>>(p, a, tb, te, mom, ready);
+}
+
+void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
+                         void* mom, uint8_t* ready, cudaStream_t s) {
+  switch (a.storage) {
+    case ST_F64: node_moments_s<double>(p, a, tb, te, mom, ready, s); break;
+    case ST_F32: node_moments_s<float>(p, a, tb, te, mom, ready, s); break;
+    case ST_F16: node_moments_s<__half>(p, a, tb, te, mom, ready, s); break;
+    default: node_moments_s<__nv_bfloat16>(p, a, tb, te, mom, ready, s); break;
   }
 }
 

@@ -30,6 +30,7 @@ LBC_SPLIT_BASE, LBC_SPLIT_INSIDE, LBC_SPLIT_OUTSIDE = 0, 1, 2
 LBC_OPT_GRAPHS = 1
 LBC_BATCH_MAX_NX = 128
 LBC_OPT_TIMING = 2
+LBC_OPT_NODE_MOMENTS = 3
 LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,
@@ -93,6 +94,7 @@ _PROTOS = {
     "lbc_box_invariants": (_S, [_P, _P, _P, _P]),
     "lbc_box_status": (_S, [_P]),
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
+    "lbc_box_get_option": (_S, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "lbc_box_launches_per_step": (C.c_int64, [_P]),
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
     "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
@@ -310,6 +312,11 @@ class Box:
 
     def set_option(self, option, value):
         check(self.lib.lbc_box_set_option(self.handle, option, value), "lbc_box_set_option")
+
+    def get_option(self, option):
+        v = C.c_int64()
+        check(self.lib.lbc_box_get_option(self.handle, option, C.byref(v)), "lbc_box_get_option")
+        return int(v.value)
 
     # --- stepping and observables
     def step(self, nsteps=1):
