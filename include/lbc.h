@@ -252,11 +252,19 @@ lbc_status lbc_box_status(const lbc_box* box);
  *                  moments per marker instead (LBC_ERR_STATE).  Default:
  *                  on when M x (stencil nodes) x (interpolations per LB
  *                  step) >= half the lattice's cells, M = max_particles.
+ *  LBC_OPT_GATHER_LANES  lanes per marker in the interpolations of the
+ *                  4- and 3-point stencils (without the per-marker node
+ *                  cache of LBC_SPLIT_INSIDE): 1, 4 (each lane sums the
+ *                  stencil rows ky = lane (mod 4), then the four parts are
+ *                  added in a fixed order), or 0 = automatic (4 while the
+ *                  markers are too few to fill the GPU one lane each).  The
+ *                  two differ only in the order of the floating-point sum.
  * Errors: LBC_ERR_ARG for an unknown option or value, LBC_ERR_STATE for a
  * batch member.  Setting an option drops the captured step graphs. */
 #define LBC_OPT_GRAPHS 1
 #define LBC_OPT_TIMING 2
 #define LBC_OPT_NODE_MOMENTS 3
+#define LBC_OPT_GATHER_LANES 4
 lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
 
 /* Current value of an option (LBC_OPT_TIMING: the event pairs reserved). */

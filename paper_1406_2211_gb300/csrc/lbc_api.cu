@@ -68,6 +68,7 @@ struct Layout {
   size_t off_home, off_sortflags;     // home tile per marker; {need, changed} per step parity
   size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
   size_t off_mom, off_mready;        // node-moment field and its ready tiles (other schemes)
+  size_t off_mbricks, off_mcount;    // bricks the field is filled in, and their count
   // rigid bodies (at most one per marker)
   size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
       off_rb_frep;
@@ -145,6 +146,8 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.has_mom = !multistep;
     L.off_mom = take(L.has_mom ? fbytes : 0);
     L.off_mready = take(L.has_mom ? (size_t)L.ntiles : 0);
+    L.off_mbricks = take(L.has_mom ? (size_t)moment_brick_count(g) * sizeof(int2) : 0);
+    L.off_mcount = take(L.has_mom ? sizeof(int) : 0);
     L.off_rb_first = take((size_t)M * 4);
     L.off_rb_count = take((size_t)M * 4);
     L.off_rb_radius = take((size_t)M * 8);
@@ -194,6 +197,7 @@ struct lbc_box {
   double rigid_k, rigid_krep;
   lbc_batch* batch;    // the batch this box belongs to, or null
   bool mom_on;         // gathers read the node-moment field (LBC_OPT_NODE_MOMENTS)
+  int gather_lanes;    // LBC_OPT_GATHER_LANES
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
   void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
@@ -292,8 +296,8 @@ struct Plan {
   void moments() {
     if (!mom_after) return;
     GatherArgs a = gather_base();
-    launch_node_moments(part_args(b), a, b->binned ? b->iptr(b->L.off_tb) : nullptr,
-                        b->iptr(b->L.off_te), b->arena + b->L.off_mom,
+    launch_node_moments(part_args(b), a, reinterpret_cast<const int2*>(b->arena + b->L.off_mbricks),
+                        b->iptr(b->L.off_mcount), b->arena + b->L.off_mom,
                         reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready), s);
     ++n;
   }
@@ -406,10 +410,18 @@ struct Plan {
     launch_sort(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
                 b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->uptr(b->L.off_key[1]),
                 b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), need, s);
+    int* mcount = b->mom_on ? b->iptr(b->L.off_mcount) : nullptr;
     launch_bins(b->L.ntiles, b->M, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
                 b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home), need,
-                changed_flag(), s);
+                changed_flag(), mcount, s);
     if (b->M > 0) n += 3 * sort_passes(kb) + 2;
+    if (mcount) {
+      // the bricks the node-moment pass fills while these bins hold
+      launch_moment_bricks(b->L.g, b->iptr(b->L.off_tb), b->iptr(b->L.off_te), need,
+                           reinterpret_cast<int2*>(b->arena + b->L.off_mbricks), mcount,
+                           reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready), s);
+      ++n;
+    }
     b->binned = true;
   }
   int* need_flag() { return b->iptr(b->L.off_sortflags) + 2 * par; }
@@ -443,6 +455,7 @@ struct Plan {
     a.nlive = b->iptr(b->L.off_nlive);
     a.ncache = b->arena + b->L.off_ncache;
     a.ncache_b = reinterpret_cast<int4*>(b->arena + b->L.off_ncache_b);
+    a.lanes = b->gather_lanes;
     if (b->mom_on) {
       a.mom = b->arena + b->L.off_mom;
       a.mready = reinterpret_cast<const uint8_t*>(b->arena + b->L.off_mready);
@@ -920,6 +933,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->nrigid = 0;
   b->rigid_k = b->rigid_krep = 0.0;
   b->mom_on = L.has_particles && L.has_mom && moments_pay(L, b->cpl, max_particles);
+  b->gather_lanes = 0;
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -931,7 +945,8 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
         cudaMemset(b->arena + L.off_mark, 0, (size_t)L.ntiles * 4) != cudaSuccess ||
         cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaMemset(b->arena + L.off_sortflags, 0, 4 * sizeof(int)) != cudaSuccess ||
-        (L.has_mom && cudaMemset(b->arena + L.off_mready, 0, (size_t)L.ntiles) != cudaSuccess)) {
+        (L.has_mom && (cudaMemset(b->arena + L.off_mready, 0, (size_t)L.ntiles) != cudaSuccess ||
+                       cudaMemset(b->arena + L.off_mcount, 0, sizeof(int)) != cudaSuccess))) {
       delete b;
       return LBC_ERR_CUDA;
     }
@@ -1305,12 +1320,21 @@ lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
     if (b->mom_on == (value == 1)) return LBC_OK;
     reset_graphs(b);
     b->mom_on = value == 1;
-    // steps taken while it was off left the field behind the populations
+    // steps taken while it was off left the field behind the populations,
+    // and sorts taken then did not list its bricks: re-bin at the next step
     if (b->mom_on) {
       CK(cudaDeviceSynchronize());
       CK(cudaMemset(b->arena + b->L.off_mready, 0, (size_t)b->L.ntiles));
+      CK(cudaMemset(b->arena + b->L.off_mcount, 0, sizeof(int)));
       CK(cudaDeviceSynchronize());
+      b->binned = false;
     }
+    return LBC_OK;
+  }
+  if (option == LBC_OPT_GATHER_LANES) {
+    if (value != 0 && value != 1 && value != 4) return LBC_ERR_ARG;
+    reset_graphs(b);
+    b->gather_lanes = (int)value;
     return LBC_OK;
   }
   return LBC_ERR_ARG;
@@ -1321,6 +1345,7 @@ lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) 
   if (option == LBC_OPT_GRAPHS) *value = b->use_graphs;
   else if (option == LBC_OPT_TIMING) *value = b->timing_cap;
   else if (option == LBC_OPT_NODE_MOMENTS) *value = b->mom_on ? 1 : 0;
+  else if (option == LBC_OPT_GATHER_LANES) *value = b->gather_lanes;
   else return LBC_ERR_ARG;
   return LBC_OK;
 }

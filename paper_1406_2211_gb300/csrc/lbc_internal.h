@@ -152,10 +152,10 @@ void launch_sort(long long M, int key_bits, const uint32_t* kin, const uint32_t*
                  uint32_t* va, uint32_t* kb, uint32_t* vb, int* hist, const int* need,
                  cudaStream_t s);
 // tile ranges, home tiles and the "bins changed" flag after a sort (same
-// condition)
+// condition); zeroes *brick_count too when it is not null
 void launch_bins(int ntiles, long long M, const uint32_t* sorted_keys, const uint32_t* idx,
                  int* tile_begin, int* tile_end, uint32_t* home, const int* need, int* changed,
-                 cudaStream_t s);
+                 int* brick_count, cudaStream_t s);
 
 enum GatherMode {
   GM_COUPLE = 0,      // force coupling / EBF / modified EBF half step
@@ -194,6 +194,7 @@ struct GatherArgs {
   // mready[tile] != 0 (the others are pulled from the populations); null:
   // unused.  The same function computes both, so the two agree bit for bit.
   const void* mom; const uint8_t* mready;
+  int lanes;            // lanes per marker of the 4- and 3-point stencils: 0 automatic, 1, 4
   // fused: the thread of slot k first runs the drift sub-step `drift` of
   // its marker (mode GM_COUPLE; positions, velocities and F_int come from it)
   int fused;
@@ -214,11 +215,19 @@ struct GatherArgs {
   int* nlive;
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
-// fills the node-moment field from a.pops in every tile within one tile of
-// a tile that holds a marker (tb / te: the bins; null: every tile), sets
-// ready[tile] to 1 there and to 0 elsewhere
-void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
-                         void* mom, uint8_t* ready, cudaStream_t s);
+// Node-moment field.  Bricks are 32 x 4 x 4 cells (eight tiles along x),
+// (tz ty_ bx) numbered with bx fastest, bx < ceil(ntx / 8).
+int moment_brick_count(const Geom& g);
+// after a re-binning (returns at once if *need == 0): lists the bricks that
+// hold a tile within one tile of a tile with markers, as (brick, 8-bit mask
+// of such tiles), appending to bricks[*count] (the count is zeroed by the
+// bins' clearing kernel), and clears ready[] of every other tile
+void launch_moment_bricks(const Geom& g, const int* tb, const int* te, const int* need,
+                          int2* bricks, int* count, uint8_t* ready, cudaStream_t s);
+// fills the field from a.pops in the masked tiles of the listed bricks and
+// sets their ready[] bytes
+void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int2* bricks,
+                         const int* count, void* mom, uint8_t* ready, cudaStream_t s);
 
 struct SpreadArgs {
   const void* rec;                            // StencilRecT<C>[M]

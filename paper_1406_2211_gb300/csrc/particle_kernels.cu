@@ -575,8 +575,9 @@ void launch_sort(long long M, int key_bits, const uint32_t* kin, const uint32_t*
 // markers get an empty range), the home tile of every marker, and the
 // "bins changed" flag
 __global__ void bins_clear_kernel(int ntiles, int* __restrict__ tb, int* __restrict__ te,
-                                  const int* need) {
+                                  const int* need, int* brick_count) {
   if (skip(need)) return;
+  if (brick_count && blockIdx.x == 0 && threadIdx.x == 0) *brick_count = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
     tb[t] = 0;
     te[t] = 0;
@@ -598,9 +599,10 @@ __global__ void bins_kernel(long long M, const uint32_t* __restrict__ keys,
 }
 
 void launch_bins(int ntiles, long long M, const uint32_t* keys, const uint32_t* idx, int* tb,
-                 int* te, uint32_t* home, const int* need, int* changed, cudaStream_t s) {
+                 int* te, uint32_t* home, const int* need, int* changed, int* brick_count,
+                 cudaStream_t s) {
   bins_clear_kernel<<<(ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024, 256, 0, s>>>(
-      ntiles, tb, te, need);
+      ntiles, tb, te, need, brick_count);
   if (M > 0) bins_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(M, keys, idx, tb, te, home, need,
                                                                      changed);
 }
@@ -666,11 +668,34 @@ __device__ inline void cache_store(double* p, const double (&j)[3], double inv) 
   reinterpret_cast<double2*>(p)[1] = make_double2(j[2], inv);
 }
 
-// fluid velocity at one stencil node (x, y, z) of weight wt, added to own:
-// (((j + c1 F1) + cg g) + c2 F2) / rho, with j and 1 / rho taken from the
-// node cache where it is valid, else from the node-moment field where its
-// tile is ready, else pulled from the populations (F1, F2 where their tile
-// flags are set)
+// velocity contribution of one stencil node of weight wt from its j and
+// 1 / rho, added to own: (((j + c1 F1) + cg g) + c2 F2) / rho (F1, F2 where
+// their tile flags are set)
+template <typename C>
+__device__ __forceinline__ void node_add(const GatherArgs& a, long long cell, int tile, C wt,
+                                         C (&j)[3], C inv, const C (&cgg)[3], C (&own)[3]) {
+  const C* F1 = static_cast<const C*>(a.F1);
+  if (F1 && a.flag1[tile]) {
+    const C c1 = rv<C>(a.c1);
+    C fx, fy, fz;
+    load_force(F1, cell, fx, fy, fz);
+    j[0] += c1 * fx; j[1] += c1 * fy; j[2] += c1 * fz;
+  }
+  j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
+  const C* F2 = static_cast<const C*>(a.F2);
+  if (F2 && a.flag2[tile]) {
+    const C c2 = rv<C>(a.c2);
+    C fx, fy, fz;
+    load_force(F2, cell, fx, fy, fz);
+    j[0] += c2 * fx; j[1] += c2 * fy; j[2] += c2 * fz;
+  }
+  own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
+}
+
+// fluid velocity at one stencil node (x, y, z) of weight wt, added to own,
+// with j and 1 / rho taken from the node cache where it is valid, else from
+// the node-moment field where its tile is ready, else pulled from the
+// populations
 template <typename S, bool WALLS>
 __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, int x, int y, int z,
                                             typename Store<S>::C wt, bool reuse,
@@ -690,38 +715,92 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
       node_base<S, WALLS>(a, g, x, y, z, j, inv);
     if (a.cache != 0) cache_store(slot, j, inv);
   }
-  const C* F1 = static_cast<const C*>(a.F1);
-  if (F1 && a.flag1[tile]) {
-    const C c1 = rv<C>(a.c1);
-    C fx, fy, fz;
-    load_force(F1, cell, fx, fy, fz);
-    j[0] += c1 * fx; j[1] += c1 * fy; j[2] += c1 * fz;
-  }
-  j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
-  const C* F2 = static_cast<const C*>(a.F2);
-  if (F2 && a.flag2[tile]) {
-    const C c2 = rv<C>(a.c2);
-    C fx, fy, fz;
-    load_force(F2, cell, fx, fy, fz);
-    j[0] += c2 * fx; j[1] += c2 * fy; j[2] += c2 * fz;
-  }
-  own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
+  node_add<C>(a, cell, tile, wt, j, inv, cgg, own);
 }
 
-// REUSE: launched for sub-steps that read the node cache or the node-moment
-// field (fewer registers, more markers in flight); the others keep registers for the population
-// loads of two nodes at a time
-template <typename S, bool WALLS, int ST, bool REUSE>
-__global__ void __launch_bounds__(GATHER_THREADS, (REUSE && sizeof(typename Store<S>::C) == 4) ? 6 : 4)
+template <typename T>
+__device__ __forceinline__ T pick(const T (&v)[4], int q) {
+  return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
+}
+template <typename T>
+__device__ __forceinline__ T pick(const T (&v)[3], int q) {
+  return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
+}
+
+// The lane's stencil nodes (the rows ky = q (mod GL) of lane q of a marker's
+// GL lanes; every row for GL = 1) read from the node-moment field, unrolled,
+// in the order of the generic loop: the same sum as there when every node's
+// tile is ready.  Returns false if one was not (own is then to be redone by
+// the generic loop; the values read there are discarded).
+template <typename S, bool WALLS, int SN, int GL>
+__device__ __forceinline__ bool gather_field(const GatherArgs& a, const Geom& g, const int (&xs)[SN],
+                                             const int (&ys)[SN], const int (&zs)[SN],
+                                             const typename Store<S>::C (&w)[3][4], int sub,
+                                             const typename Store<S>::C (&cgg)[3],
+                                             typename Store<S>::C (&own)[3]) {
+  using C = typename Store<S>::C;
+  const C* mom = static_cast<const C*>(a.mom);
+  constexpr int NR = GL == 1 ? SN : (SN + GL - 1) / GL;    // rows per lane
+  bool ok = true;
+  int txs[SN];
+#pragma unroll
+  for (int q = 0; q < SN; ++q) txs[q] = xs[q] >> TILE_SHIFT;
+#pragma unroll
+  for (int kz = 0; kz < SN; ++kz) {
+    if (WALLS && zs[kz] < 0) continue;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      int y;
+      C wy;
+      if constexpr (GL == 1) {
+        y = ys[r]; wy = w[1][r];
+      } else {
+        const int ky = sub + r * GL;
+        if (ky >= SN) continue;
+        y = pick(ys, ky); wy = pick(w[1], ky);
+      }
+      const C wyz = wy * w[2][kz];
+      const int trow = ((zs[kz] >> TILE_SHIFT) * g.nty + (y >> TILE_SHIFT)) * g.ntx;
+      const long long crow = zs[kz] * g.plane + (long long)y * g.pitch;
+#pragma unroll
+      for (int kx = 0; kx < SN; ++kx) {
+        const long long cell = crow + xs[kx];
+        const int tile = trow + txs[kx];
+        ok &= a.mready[tile] != 0;
+        C j[3], inv;
+        cache_load(mom + 4 * cell, j, inv);
+        node_add<C>(a, cell, tile, w[0][kx] * wyz, j, inv, cgg, own);
+      }
+    }
+  }
+  return ok;
+}
+
+// Variants (VAR): GV_FULL keeps registers for the population loads of two
+// nodes at a time; GV_LIGHT is launched for sub-steps that read the node
+// cache or the node-moment field (fewer registers, more markers in flight);
+// GV_QUAD (4- and 3-point stencils, no node cache, no fused drift; by
+// default only for fewer markers than the one-lane variants keep resident
+// at once) gives each marker four lanes, lane q taking the stencil rows ky = q (mod 4) of
+// every plane, and sums their parts with a fixed butterfly: four times the
+// loads in flight for the same markers.  Lane 0 of a group does the
+// marker's update and writes its record; the tile claims are shared out by
+// plane.
+constexpr int GV_FULL = 0, GV_LIGHT = 1, GV_QUAD = 2;
+
+template <typename S, bool WALLS, int ST, int VAR>
+__global__ void __launch_bounds__(GATHER_THREADS, (VAR == GV_LIGHT && sizeof(typename Store<S>::C) == 4) ? 6 : 4)
 gather_kernel(const PartArgs p, const GatherArgs a) {
   using C = typename Store<S>::C;
   constexpr int SN = nodes_1d<ST>();
+  constexpr int GL = VAR == GV_QUAD ? 4 : 1;       // lanes per marker
   const Geom& g = p.g;
   const long long M = p.M;
   const int lane = threadIdx.x & 31;
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool active = k < M;
-  if (!active) return;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long k = gid / GL;
+  const int sub = (int)(gid % GL);
+  if (k >= M) return;                  // whole groups leave together
   const long long i = a.perm ? (long long)a.perm[k] : k;
   const int n3[3] = {g.nx, g.ny, g.nz};
   const bool per[3] = {true, true, !g.walls};
@@ -733,7 +812,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
   C Fi[3] = {C(0), C(0), C(0)};
   double X[3];
   const bool at_aux = a.mode == GM_IBM_HALF || a.mode == GM_IBM_FINAL;
-  if (a.fused) {
+  if (GL == 1 && a.fused) {
     C F[3];
     drift_one<C>(p, a.drift, i, X, v, F);
     im = a.inv_mass[i];
@@ -777,13 +856,21 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
     const C cgg[3] = {rv<C>(a.cgg[0]), rv<C>(a.cgg[1]), rv<C>(a.cgg[2])};
     C* nc = static_cast<C*>(a.ncache);
     bool reuse = false;
-    if (a.cache == 2 && (a.invalidate == nullptr || *a.invalidate == 0)) {
+    if (GL == 1 && a.cache == 2 && (a.invalidate == nullptr || *a.invalidate == 0)) {
       const int4 cb = a.ncache_b[k];
       reuse = cb.x == b[0] && cb.y == b[1] && cb.z == b[2];
     }
-    if (a.cache != 0 && !reuse) a.ncache_b[k] = make_int4(b[0], b[1], b[2], 0);
+    if (GL == 1 && a.cache != 0 && !reuse) a.ncache_b[k] = make_int4(b[0], b[1], b[2], 0);
+    bool done = false;
+    if constexpr (GL > 1) {
+      if (a.mom != nullptr) {
+        done = gather_field<S, WALLS, SN, GL>(a, g, xs, ys, zs, w, sub, cgg, own);
+        if (!done) own[0] = own[1] = own[2] = C(0);
+      }
+    }
     // node (kx, ky, kz) of slot k sits at nc[((kz SN + ky) SN + kx) M + k] (x 4)
-    if (SN == 2) {
+    if (done) {
+    } else if (SN == 2) {
 #pragma unroll
       for (int kz = 0; kz < SN; ++kz)
 #pragma unroll
@@ -800,7 +887,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       for (int kz = 0; kz < SN; ++kz) {
         if (WALLS && zs[kz] < 0) continue;
 #pragma unroll 1
-        for (int ky = 0; ky < SN; ++ky) {
+        for (int ky = sub; ky < SN; ky += GL) {
           const C wyz = w[1][ky] * w[2][kz];
 #pragma unroll 2
           for (int kx = 0; kx < SN; ++kx) {
@@ -811,12 +898,22 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       }
     }
   }
+  // the warp's lanes still running are its first nact (whole groups)
+  const long long wbase = gid - lane;
+  const int nact = M * GL - wbase >= 32 ? 32 : (int)(M * GL - wbase);
+  const unsigned am = nact == 32 ? 0xffffffffu : ((1u << nact) - 1u);
+  if (GL > 1) {
+#pragma unroll
+    for (int off = 1; off < GL; off <<= 1)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) own[c] += __shfl_xor_sync(am, own[c], off);
+  }
 
   // ---- own marker: coupling / advection update (FP64 integration),
   // stencil record and tile claims
   const double s = a.s.d;
   C Frec[3] = {C(0), C(0), C(0)};
-  switch (a.mode) {
+  switch (sub == 0 ? a.mode : -1) {
     case GM_COUPLE: {
       C dv[3];
       for (int c = 0; c < 3; ++c) dv[c] = (C)(v[c] - (double)own[c]);
@@ -868,13 +965,15 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
     int nclaim = 0;
     int tq[3][SN];
     {
-      StencilRecT<C> r;
-      r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
-      for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
-      r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
-      r.pad = C(0);
-      static_cast<StencilRecT<C>*>(a.rec)[k] = r;
-      a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+      if (sub == 0) {
+        StencilRecT<C> r;
+        r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
+        for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
+        r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
+        r.pad = C(0);
+        static_cast<StencilRecT<C>*>(a.rec)[k] = r;
+        a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+      }
       // claim the tiles the stencil reaches (nodes with non-zero weight); per
       // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
       // node's tile or carries no weight
@@ -899,14 +998,14 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
         for (int qy = 0; qy < SN; ++qy)
 #pragma unroll
           for (int qx = 0; qx < SN; ++qx)
-            if (tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
+            if (qz % GL == sub && tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
               uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
               if (atomicExch(m, 1u) == 0u) {
                 claimed |= 1ull << ((qz * SN + qy) * SN + qx);
                 ++nclaim;
               }
             }
-      if (a.keys) {
+      if (a.keys && sub == 0) {
         // the bins are valid while every stencil node lies within three
         // cells of the home tile (the reach of the spreading's neighbour
         // search)
@@ -920,11 +1019,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
         if (!ok) *a.status = 1;
       }
     }
-    // list slots for the claimed tiles, one atomic per warp; the lanes still
-    // running are the warp's first nact lanes (slots k < M)
-    const long long kw = k - lane;
-    const int nact = M - kw >= 32 ? 32 : (int)(M - kw);
-    const unsigned am = nact == 32 ? 0xffffffffu : ((1u << nact) - 1u);
+    // list slots for the claimed tiles, one atomic per warp
     int incl = nclaim;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -947,21 +1042,42 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
   }
 }
 
-template <typename S, bool WALLS, bool REUSE>
+template <typename S, bool WALLS, int VAR>
 static void gather_str(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
   const int bs = GATHER_THREADS;                // one marker per thread
   const unsigned nb = (unsigned)((p.M + bs - 1) / bs);
-  if (p.stencil == 0) gather_kernel<S, WALLS, 0, REUSE><<<nb, bs, 0, s>>>(p, a);
-  else if (p.stencil == 1) gather_kernel<S, WALLS, 1, REUSE><<<nb, bs, 0, s>>>(p, a);
-  else gather_kernel<S, WALLS, 2, REUSE><<<nb, bs, 0, s>>>(p, a);
+  if (p.stencil == 0) gather_kernel<S, WALLS, 0, VAR><<<nb, bs, 0, s>>>(p, a);
+  else if (p.stencil == 1) gather_kernel<S, WALLS, 1, VAR><<<nb, bs, 0, s>>>(p, a);
+  else gather_kernel<S, WALLS, 2, VAR><<<nb, bs, 0, s>>>(p, a);
+}
+
+// markers the one-lane variants keep resident at once (6 blocks of 128
+// threads per SM); below that the four-lane variant fills the GPU better
+static long long one_lane_wave() {
+  static long long w = 0;
+  if (w == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    w = (long long)(sms > 0 ? sms : 1) * 6 * GATHER_THREADS;
+  }
+  return w;
 }
 
 template <typename S, bool WALLS>
 static void gather_st(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
+  const bool quad_ok = p.stencil != 0 && a.cache == 0 && !a.fused;
+  if (quad_ok && (a.lanes == 4 || (a.lanes == 0 && p.M < one_lane_wave()))) {
+    const int bs = GATHER_THREADS;              // four lanes per marker
+    const unsigned nb = (unsigned)((4 * p.M + bs - 1) / bs);
+    if (p.stencil == 1) gather_kernel<S, WALLS, 1, GV_QUAD><<<nb, bs, 0, s>>>(p, a);
+    else gather_kernel<S, WALLS, 2, GV_QUAD><<<nb, bs, 0, s>>>(p, a);
+    return;
+  }
   // the lighter variant spills with the wall bounce-back of the pull, which
   // the field reads still need where a tile is not ready
-  if (a.cache == 2 || (a.mom != nullptr && !WALLS)) gather_str<S, WALLS, true>(p, a, s);
-  else gather_str<S, WALLS, false>(p, a, s);
+  if (a.cache == 2 || (a.mom != nullptr && !WALLS)) gather_str<S, WALLS, GV_LIGHT>(p, a, s);
+  else gather_str<S, WALLS, GV_FULL>(p, a, s);
 }
 
 template <typename S>
@@ -980,71 +1096,132 @@ void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ node moments
-// One block per brick of 32 x 4 x 4 cells (eight tiles along x), two cells
-// per thread along z; a warp covers 32 consecutive cells of one row, as in
-// the LB step.  A tile is filled when one of its 27 neighbour tiles (itself
-// included; periodic in x and y, and in z without walls) holds a marker: a
-// marker stays within about a cell of its home tile between re-binnings and
-// its stencil reaches two cells beyond its own, so the gathers find nearly
-// every node in such a tile; a node in a tile that is not ready is pulled
-// from the populations instead.  Without bins every tile is filled.
+// The field is filled in bricks of 32 x 4 x 4 cells (eight tiles along x):
+// a warp covers 32 consecutive cells of one row, as in the LB step.  The
+// bricks are listed at each re-binning with the tiles that lie within one
+// tile of a tile holding a marker (periodic in x and y, and in z without
+// walls): a marker stays within about a cell of its home tile between
+// re-binnings and its stencil reaches two cells beyond its own, so the
+// gathers find nearly every node in such a tile; a node in a tile that is
+// not ready is pulled from the populations instead.
 constexpr int MOM_THREADS = 256;
 
-template <typename S, bool WALLS>
-__global__ void __launch_bounds__(MOM_THREADS)
-node_moments_kernel(const PartArgs p, const GatherArgs a, const int* __restrict__ tb,
-                    const int* __restrict__ te, void* mom, uint8_t* __restrict__ ready) {
-  using C = typename Store<S>::C;
-  const Geom& g = p.g;
-  __shared__ int need[8];
-  const int t = threadIdx.x;
-  const int tx0 = blockIdx.x * 8, ty = blockIdx.y, tz = blockIdx.z;
-  if (t < 8) need[t] = tb == nullptr ? 1 : 0;
-  __syncthreads();
-  if (tb != nullptr && t < 8 * 27 && tx0 + t / 27 < g.ntx) {
-    const int d = t % 27;
-    const int nx = wrap_int(tx0 + t / 27 + d % 3 - 1, g.ntx);
-    const int ny = wrap_int(ty + (d / 3) % 3 - 1, g.nty);
-    int nz = tz + d / 9 - 1;
-    bool in = true;
-    if (WALLS) in = nz >= 0 && nz < g.ntz;
-    else nz = wrap_int(nz, g.ntz);
-    if (in) {
-      const int n = (nz * g.nty + ny) * g.ntx + nx;
-      if (te[n] > tb[n]) need[t / 27] = 1;
+int moment_brick_count(const Geom& g) { return ((g.ntx + 7) >> 3) * g.nty * g.ntz; }
+
+// one thread per tile, eight consecutive lanes per brick (the row of tiles
+// is padded to a multiple of eight)
+__global__ void moment_bricks_kernel(const Geom g, const int* __restrict__ tb,
+                                     const int* __restrict__ te, const int* need,
+                                     int2* __restrict__ bricks, int* count,
+                                     uint8_t* __restrict__ ready) {
+  if (skip(need)) return;
+  const int nbx = (g.ntx + 7) >> 3;
+  const long long row = 8LL * nbx;
+  const long long total = row * g.nty * g.ntz;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int tx = 0, ty = 0, tz = 0;
+  bool needed = false;
+  if (gid < total) {
+    tx = (int)(gid % row);
+    const long long r = gid / row;
+    ty = (int)(r % g.nty);
+    tz = (int)(r / g.nty);
+    if (tx < g.ntx) {
+      for (int d = 0; d < 27 && !needed; ++d) {
+        const int nx = wrap_int(tx + d % 3 - 1, g.ntx);
+        const int ny = wrap_int(ty + (d / 3) % 3 - 1, g.nty);
+        int nz = tz + d / 9 - 1;
+        if (g.walls) {
+          if (nz < 0 || nz >= g.ntz) continue;
+        } else {
+          nz = wrap_int(nz, g.ntz);
+        }
+        const int n = (nz * g.nty + ny) * g.ntx + nx;
+        needed = te[n] > tb[n];
+      }
+      if (!needed) ready[(tz * g.nty + ty) * g.ntx + tx] = 0;
     }
   }
-  __syncthreads();
-  if (t < 8 && tx0 + t < g.ntx) ready[(tz * g.nty + ty) * g.ntx + tx0 + t] = (uint8_t)need[t];
-  const int x = blockIdx.x * 32 + (t & 31);
-  const int y = ty * TILE + ((t >> 5) & 3);
-  if (x >= g.nx || y >= g.ny || !need[(t & 31) >> TILE_SHIFT]) return;
-  C* out = static_cast<C*>(mom);
-#pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const int z = tz * TILE + 2 * (t >> 7) + h;
-    if (z >= g.nz) break;
-    C j[3], inv;
-    node_base<S, WALLS>(a, g, x, y, z, j, inv);
-    cache_store(out + 4 * (z * g.plane + (long long)y * g.pitch + x), j, inv);
+  const unsigned bal = __ballot_sync(0xffffffffu, needed);
+  const int lane = threadIdx.x & 31;
+  if (gid < total && (lane & 7) == 0) {
+    const int m = (int)((bal >> lane) & 0xFFu);
+    if (m) {
+      const int e = atomicAdd(count, 1);
+      bricks[e] = make_int2((tz * g.nty + ty) * nbx + tx / 8, m);
+    }
   }
+}
+
+void launch_moment_bricks(const Geom& g, const int* tb, const int* te, const int* need,
+                          int2* bricks, int* count, uint8_t* ready, cudaStream_t s) {
+  const long long total = 8LL * ((g.ntx + 7) >> 3) * g.nty * g.ntz;
+  moment_bricks_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, tb, te, need, bricks,
+                                                                       count, ready);
+}
+
+// persistent: each block takes the listed bricks in turn, two cells per
+// thread along z
+template <typename S, bool WALLS>
+__global__ void __launch_bounds__(MOM_THREADS)
+node_moments_kernel(const PartArgs p, const GatherArgs a, const int2* __restrict__ bricks,
+                    const int* count, void* mom, uint8_t* __restrict__ ready) {
+  using C = typename Store<S>::C;
+  const Geom& g = p.g;
+  const int nb = *count;
+  const int nbx = (g.ntx + 7) >> 3;
+  const int t = threadIdx.x;
+  C* out = static_cast<C*>(mom);
+  for (int e = blockIdx.x; e < nb; e += gridDim.x) {
+    const int2 br = bricks[e];
+    const int bx = br.x % nbx, ty = (br.x / nbx) % g.nty, tz = br.x / (nbx * g.nty);
+    if (t < 8 && ((br.y >> t) & 1)) ready[(tz * g.nty + ty) * g.ntx + bx * 8 + t] = 1;
+    const int x = bx * 32 + (t & 31);
+    const int y = ty * TILE + ((t >> 5) & 3);
+    if (x >= g.nx || y >= g.ny || !((br.y >> ((t & 31) >> TILE_SHIFT)) & 1)) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int z = tz * TILE + 2 * (t >> 7) + h;
+      if (z < g.nz) {
+        C j[3], inv;
+        node_base<S, WALLS>(a, g, x, y, z, j, inv);
+        cache_store(out + 4 * (z * g.plane + (long long)y * g.pitch + x), j, inv);
+      }
+    }
+  }
+}
+
+template <typename S, bool WALLS>
+static void node_moments_sw(const PartArgs& p, const GatherArgs& a, const int2* bricks,
+                            const int* count, void* mom, uint8_t* ready, cudaStream_t s) {
+  static int grid = 0;          // resident blocks on the whole GPU
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, node_moments_kernel<S, WALLS>,
+                                                  MOM_THREADS, 0);
+    grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  const int nb = moment_brick_count(p.g);
+  node_moments_kernel<S, WALLS><<<(unsigned)(nb < grid ? nb : grid), MOM_THREADS, 0, s>>>(
+      p, a, bricks, count, mom, ready);
 }
 
 template <typename S>
-static void node_moments_s(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
-                           void* mom, uint8_t* ready, cudaStream_t s) {
-  const dim3 grid((unsigned)((p.g.nx + 31) / 32), (unsigned)p.g.nty, (unsigned)p.g.ntz);
-  if (p.g.walls) node_moments_kernel<S, true><<<grid, MOM_THREADS, 0, s>>>(p, a, tb, te, mom, ready);
-  else node_moments_kernel<S, false><<<grid, MOM_THREADS, 0, s>>>(p, a, tb, te, mom, ready);
+static void node_moments_s(const PartArgs& p, const GatherArgs& a, const int2* bricks,
+                           const int* count, void* mom, uint8_t* ready, cudaStream_t s) {
+  if (p.g.walls) node_moments_sw<S, true>(p, a, bricks, count, mom, ready, s);
+  else node_moments_sw<S, false>(p, a, bricks, count, mom, ready, s);
 }
 
-void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int* tb, const int* te,
-                         void* mom, uint8_t* ready, cudaStream_t s) {
+void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int2* bricks,
+                         const int* count, void* mom, uint8_t* ready, cudaStream_t s) {
   switch (a.storage) {
-    case ST_F64: node_moments_s<double>(p, a, tb, te, mom, ready, s); break;
-    case ST_F32: node_moments_s<float>(p, a, tb, te, mom, ready, s); break;
-    case ST_F16: node_moments_s<__half>(p, a, tb, te, mom, ready, s); break;
-    default: node_moments_s<__nv_bfloat16>(p, a, tb, te, mom, ready, s); break;
+    case ST_F64: node_moments_s<double>(p, a, bricks, count, mom, ready, s); break;
+    case ST_F32: node_moments_s<float>(p, a, bricks, count, mom, ready, s); break;
+    case ST_F16: node_moments_s<__half>(p, a, bricks, count, mom, ready, s); break;
+    default: node_moments_s<__nv_bfloat16>(p, a, bricks, count, mom, ready, s); break;
   }
 }
 

@@ -31,6 +31,7 @@ LBC_OPT_GRAPHS = 1
 LBC_BATCH_MAX_NX = 128
 LBC_OPT_TIMING = 2
 LBC_OPT_NODE_MOMENTS = 3
+LBC_OPT_GATHER_LANES = 4
 LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,

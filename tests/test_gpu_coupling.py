@@ -52,8 +52,14 @@ SCHEMES = [
 
 @pytest.mark.parametrize("kind,order,split,n,stencil", SCHEMES)
 @pytest.mark.parametrize("walls", [False, True])
-def test_coupled_steps_match_oracle(kind, order, split, n, stencil, walls):
+@pytest.mark.parametrize("lanes", [4, 1])
+def test_coupled_steps_match_oracle(kind, order, split, n, stencil, walls, lanes):
+    """lanes: markers per lane group of the 4- and 3-point interpolation
+    (both variants against the oracle)."""
     require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    if lanes == 1 and (stencil == "trilinear" or split == "inside"):
+        pytest.skip("these interpolations always run one lane per marker")
     shape = (11, 10, 12)
     fbar0 = synth.random_populations(shape, seed=21, amp=1e-3)
     parts = _particles(shape, kind, seed=5)
@@ -63,6 +69,7 @@ def test_coupled_steps_match_oracle(kind, order, split, n, stencil, walls):
     box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=(1e-5, 0, -1e-5),
                         walls=walls, uw=uw, storage="f64", kind=kind, order=order,
                         stencil=stencil, gamma=1.7, split=split, n=n, parts=parts)
+    box.set_option(lbc.LBC_OPT_GATHER_LANES, lanes)
     for nsteps in (1, 2, 3):
         box.step(nsteps)
         for _ in range(nsteps):
