@@ -718,20 +718,21 @@ __device__ __forceinline__ void gather_node(const GatherArgs& a, const Geom& g, 
   node_add<C>(a, cell, tile, wt, j, inv, cgg, own);
 }
 
-template <typename T>
-__device__ __forceinline__ T pick(const T (&v)[4], int q) {
-  return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
-}
-template <typename T>
-__device__ __forceinline__ T pick(const T (&v)[3], int q) {
-  return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
+// v[q] by selects (the array stays in registers)
+template <typename T, int N>
+__device__ __forceinline__ T pick(const T (&v)[N], int q) {
+  T r = v[0];
+#pragma unroll
+  for (int e = 1; e < N; ++e) r = q == e ? v[e] : r;
+  return r;
 }
 
 // The lane's stencil nodes (the rows ky = q (mod GL) of lane q of a marker's
-// GL lanes; every row for GL = 1) read from the node-moment field, unrolled,
-// in the order of the generic loop: the same sum as there when every node's
-// tile is ready.  Returns false if one was not (own is then to be redone by
-// the generic loop; the values read there are discarded).
+// GL lanes; every row for GL = 1) read from the node-moment field in the
+// order of the generic loop, with the cell and tile offsets of a row taken
+// once: the same sum as there when every node's tile is ready.  Returns
+// false if one was not (own is then to be redone by the generic loop; the
+// values read here are discarded).
 template <typename S, bool WALLS, int SN, int GL>
 __device__ __forceinline__ bool gather_field(const GatherArgs& a, const Geom& g, const int (&xs)[SN],
                                              const int (&ys)[SN], const int (&zs)[SN],
@@ -740,28 +741,23 @@ __device__ __forceinline__ bool gather_field(const GatherArgs& a, const Geom& g,
                                              typename Store<S>::C (&own)[3]) {
   using C = typename Store<S>::C;
   const C* mom = static_cast<const C*>(a.mom);
-  constexpr int NR = GL == 1 ? SN : (SN + GL - 1) / GL;    // rows per lane
   bool ok = true;
   int txs[SN];
 #pragma unroll
   for (int q = 0; q < SN; ++q) txs[q] = xs[q] >> TILE_SHIFT;
-#pragma unroll
+#pragma unroll 1
   for (int kz = 0; kz < SN; ++kz) {
-    if (WALLS && zs[kz] < 0) continue;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      int y;
-      C wy;
-      if constexpr (GL == 1) {
-        y = ys[r]; wy = w[1][r];
-      } else {
-        const int ky = sub + r * GL;
-        if (ky >= SN) continue;
-        y = pick(ys, ky); wy = pick(w[1], ky);
-      }
-      const C wyz = wy * w[2][kz];
-      const int trow = ((zs[kz] >> TILE_SHIFT) * g.nty + (y >> TILE_SHIFT)) * g.ntx;
-      const long long crow = zs[kz] * g.plane + (long long)y * g.pitch;
+    const int z = pick(zs, kz);
+    if (WALLS && z < 0) continue;
+    const C wz = pick(w[2], kz);
+    const long long cz = z * g.plane;
+    const int tz = (z >> TILE_SHIFT) * g.nty;
+#pragma unroll 1
+    for (int ky = sub; ky < SN; ky += GL) {
+      const int y = pick(ys, ky);
+      const C wyz = pick(w[1], ky) * wz;
+      const long long crow = cz + (long long)y * g.pitch;
+      const int trow = (tz + (y >> TILE_SHIFT)) * g.ntx;
 #pragma unroll
       for (int kx = 0; kx < SN; ++kx) {
         const long long cell = crow + xs[kx];
@@ -862,11 +858,9 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
     }
     if (GL == 1 && a.cache != 0 && !reuse) a.ncache_b[k] = make_int4(b[0], b[1], b[2], 0);
     bool done = false;
-    if constexpr (GL > 1) {
-      if (a.mom != nullptr) {
-        done = gather_field<S, WALLS, SN, GL>(a, g, xs, ys, zs, w, sub, cgg, own);
-        if (!done) own[0] = own[1] = own[2] = C(0);
-      }
+    if (a.mom != nullptr && a.cache == 0) {
+      done = gather_field<S, WALLS, SN, GL>(a, g, xs, ys, zs, w, sub, cgg, own);
+      if (!done) own[0] = own[1] = own[2] = C(0);
     }
     // node (kx, ky, kz) of slot k sits at nc[((kz SN + ky) SN + kx) M + k] (x 4)
     if (done) {
@@ -883,16 +877,22 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
             gather_node<S, WALLS>(a, g, xs[kx], ys[ky], zs[kz], wt, reuse, slot, cgg, own);
           }
     } else {
+      // the loops are not unrolled: the per-axis nodes and weights are
+      // picked by selects, which keeps them in registers
 #pragma unroll 1
       for (int kz = 0; kz < SN; ++kz) {
-        if (WALLS && zs[kz] < 0) continue;
+        const int z = pick(zs, kz);
+        if (WALLS && z < 0) continue;
+        const C wz = pick(w[2], kz);
 #pragma unroll 1
         for (int ky = sub; ky < SN; ky += GL) {
-          const C wyz = w[1][ky] * w[2][kz];
+          const int y = pick(ys, ky);
+          const C wyz = pick(w[1], ky) * wz;
 #pragma unroll 2
           for (int kx = 0; kx < SN; ++kx) {
             C* slot = nc + (((kz * SN + ky) * SN + kx) * M + k) * 4;
-            gather_node<S, WALLS>(a, g, xs[kx], ys[ky], zs[kz], w[0][kx] * wyz, reuse, slot, cgg, own);
+            gather_node<S, WALLS>(a, g, pick(xs, kx), y, z, pick(w[0], kx) * wyz, reuse, slot, cgg,
+                                  own);
           }
         }
       }
