@@ -335,15 +335,21 @@ def other_workload_boxes(name, storage):
     return box, nx * ny * nz, desc
 
 
-def run_other_workloads(args, peak):
-    """The shell and rigid-sphere workloads at full size: coupled MLUPS over
-    `steps` steps (CUDA events) and the LB kernel's fraction of the peak."""
+OTHER_WORKLOADS = (("cfg3_ibm_shells_192", ("f32", "bf16dev")),
+                   ("cfg4_mebf_spheres_128", ("f32",)))
+
+
+def run_other_workloads(args, peak, only=None):
+    """The shell and rigid-sphere workloads at full size (or only the one
+    named): coupled MLUPS over `steps` steps (CUDA events, at most 60) and the
+    LB kernel's fraction of the peak."""
     import torch
     from paper_1406_2211_gb300 import lbc
     out = {}
     steps = min(args.steps, 60)
-    for name, storages in (("cfg3_ibm_shells_192", ("f32", "bf16dev")),
-                           ("cfg4_mebf_spheres_128", ("f32",))):
+    for name, storages in OTHER_WORKLOADS:
+        if only is not None and name != only:
+            continue
         out[name] = {}
         for st in storages:
             box, cells, desc = other_workload_boxes(name, st)
@@ -524,6 +530,9 @@ def main():
     # box edge / SCALE and particle count / SCALE^3 at the same densities: the
     # small case for multi-pass profiler captures (default: the full workload)
     ap.add_argument("--scale", type=int, default=1)
+    # only the full-size shell or rigid-sphere workload (its own JSON line;
+    # for launch lists of that workload)
+    ap.add_argument("--workload", default=None, choices=[n for n, _ in OTHER_WORKLOADS])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -535,6 +544,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return 0
+    if args.workload is not None:
+        if rank == 0:
+            res = run_other_workloads(args, measured_peaks()[0], only=args.workload)
+            print(json.dumps({"workload": args.workload, "results": res[args.workload]}))
         return 0
 
     if world > 1:

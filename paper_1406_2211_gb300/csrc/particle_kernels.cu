@@ -1000,7 +1000,9 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
           for (int qx = 0; qx < SN; ++qx)
             if (qz % GL == sub && tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
               uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
-              if (atomicExch(m, 1u) == 0u) {
+              // most tiles are claimed already: an L2 read (marks only go
+              // from 0 to 1 during the gather) spares their atomic
+              if (__ldcg(m) == 0u && atomicExch(m, 1u) == 0u) {
                 claimed |= 1ull << ((qz * SN + qy) * SN + qx);
                 ++nclaim;
               }
