@@ -1350,10 +1350,36 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   // tiles no stencil reaches keep their flag when accumulating and are
   // cleared otherwise; the marks are consumed (the live tiles are other
   // tiles, so the warps go on without waiting for each other)
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
-       t += (long long)gridDim.x * blockDim.x) {
-    if (a.mark[t] != 0u) a.mark[t] = 0u;
-    else if (!a.accumulate) a.flag[t] = 0;
+  {
+    // four tiles per thread and access (marks and flags start 256-byte
+    // aligned), the remainder one by one
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long n4 = ntiles / 4;
+    uint4* mark4 = reinterpret_cast<uint4*>(a.mark);
+    uchar4* flag4 = reinterpret_cast<uchar4*>(a.flag);
+    for (long long q = gt; q < n4; q += nthreads) {
+      const uint4 m = mark4[q];
+      const bool any = (m.x | m.y | m.z | m.w) != 0u;
+      if (any) mark4[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (!a.accumulate) {
+        if (!any) {
+          flag4[q] = make_uchar4(0, 0, 0, 0);
+        } else {
+          // a live tile's flag is set by the warp that spreads it: only
+          // the other flags are written
+          uint8_t* f = a.flag + 4 * q;
+          if (!m.x) f[0] = 0;
+          if (!m.y) f[1] = 0;
+          if (!m.z) f[2] = 0;
+          if (!m.w) f[3] = 0;
+        }
+      }
+    }
+    for (long long t = 4 * n4 + gt; t < ntiles; t += nthreads) {
+      if (a.mark[t] != 0u) a.mark[t] = 0u;
+      else if (!a.accumulate) a.flag[t] = 0;
+    }
   }
   const int nlive = __shfl_sync(0xffffffffu, lane == 0 ? *a.nlive : 0, 0);
   const int cxl = lane & 3, cyl = (lane >> 2) & 3, czl = lane >> 4;
