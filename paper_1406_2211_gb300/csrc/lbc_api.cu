@@ -108,7 +108,7 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_pos[0] = take(v3); L.off_pos[1] = take(v3);
     L.off_vel[0] = take(v3); L.off_vel[1] = take(v3);
     const size_t c3 = 3 * (size_t)M * force_elem_bytes(l->storage);   // [3][M] compute type
-    L.off_fint = take(c3); L.off_fh = take(v3); L.off_aux = take(v3);
+    L.off_fint = take(c3); L.off_fh = take(c3); L.off_aux = take(v3);
     L.off_mass = take((size_t)M * sizeof(double));
     L.off_ext = take(c3);
     for (int k = 0; k < 2; ++k) {
@@ -445,7 +445,7 @@ struct Plan {
     a.aux = b->dptr(b->L.off_aux);
     a.fint = b->arena + b->L.off_fint;
     a.inv_mass = b->dptr(b->L.off_inv_mass);
-    a.fh_out = b->dptr(b->L.off_fh);
+    a.fh_out = b->arena + b->L.off_fh;
     a.rec = b->arena + b->L.off_rec;
     a.reach = reinterpret_cast<short4*>(b->arena + b->L.off_reach);
     a.keys = b->uptr(b->L.off_key[0]);
@@ -1183,7 +1183,7 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
     r0sq[q] = nr[q] * nr[q];
   }
   CK(cudaMemcpyAsync(b->arena + b->L.off_ext, ext_c.data(), ext_c.size(), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(b->dptr(b->L.off_fh), 0, 3 * M * 8, s));
+  CK(cudaMemsetAsync(b->arena + b->L.off_fh, 0, 3 * M * force_elem_bytes(b->lat.storage), s));
   CK(cudaMemsetAsync(b->arena + b->L.off_fint, 0, 3 * M * ce, s));
   CK(cudaMemcpyAsync(b->iptr(b->L.off_nbr_start), start.data(), start.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(b->iptr(b->L.off_nbr_j), nj.data(), nj.size() * 4, cudaMemcpyHostToDevice, s));
@@ -1256,6 +1256,15 @@ lbc_status lbc_box_get_particles(lbc_box* b, double* pos, double* vel, double* f
   double* outs[3] = {pos, vel, fh};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
+    if (k == 2 && force_elem_bytes(b->lat.storage) == 4) {
+      // F^h is kept in the compute type (FP32): widened exactly here
+      std::vector<float> tf(3 * M);
+      CK(cudaMemcpyAsync(tf.data(), b->arena + offs[k], 3 * M * 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int64_t i = 0; i < M; ++i)
+        for (int c = 0; c < 3; ++c) outs[k][3 * i + c] = (double)tf[c * M + i];
+      continue;
+    }
     CK(cudaMemcpyAsync(tmp.data(), b->dptr(offs[k]), 3 * M * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     for (int64_t i = 0; i < M; ++i)

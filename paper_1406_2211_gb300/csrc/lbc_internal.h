@@ -204,7 +204,8 @@ struct GatherArgs {
   const uint32_t* keys;           // sorted home tile of each slot (null: no check)
   double* pos; double* aux; double* vel;
   const void* fint;               // [3][M] intrinsic forces, compute type
-  const double* inv_mass; double* fh_out;
+  const double* inv_mass;
+  void* fh_out;                   // [3][M] coupling force F^h, compute type
   void* rec;                      // StencilRecT<C>[M], by sorted slot
   short4* reach;                  // stencil base per sorted slot (x, y, z)
   int* status;                    // set to 1 if a marker left its home tile +- 1 cell

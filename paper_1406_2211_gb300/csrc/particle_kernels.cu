@@ -915,8 +915,10 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
   C Frec[3] = {C(0), C(0), C(0)};
   switch (sub == 0 ? a.mode : -1) {
     case GM_COUPLE: {
+      // slip v - u(X) in the compute type (FP64 work being scarce): with
+      // FP32 the rounding of v adds at most 2^-24 |v| to it
       C dv[3];
-      for (int c = 0; c < 3; ++c) dv[c] = (C)(v[c] - (double)own[c]);
+      for (int c = 0; c < 3; ++c) dv[c] = (C)v[c] - own[c];
       C Fh[3];
       const C cs = rv<C>(a.s), cim = C(im), crho = rv<C>(a.rho0);
       if (a.kind == 4) {                      // modified EBF, Eq. [modified-ebf]
@@ -937,7 +939,7 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
       const double kick = s * im;
       for (int c = 0; c < 3; ++c) {
         a.vel[c * M + i] = v[c] + kick * (double)(Fh[c] + Fi[c]);
-        if (a.fh_out) a.fh_out[c * M + i] = (double)Fh[c];
+        if (a.fh_out) static_cast<C*>(a.fh_out)[c * M + i] = Fh[c];
         Frec[c] = -rv<C>(a.rec_weight) * Fh[c];
       }
       break;
