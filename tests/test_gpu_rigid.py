@@ -101,3 +101,48 @@ def test_rigid_spheres_reduced_fp32():
     assert rel_l2(v, sm.parts.vel) < 1e-4
     rho, u = box.get_fields()
     assert rel_l2(u, sm.fluid_velocity()) < 1e-4
+
+
+def test_many_bodies_repel_across_the_periodic_boundary():
+    """More bodies than a warp has lanes (each body's warp strides over the
+    others), some pairs closer than one unit across the periodic faces
+    (minimum image in the float screen and the double force)."""
+    require_cuda()
+    shape = (24, 24, 24)
+    L = 24.0
+    rng = np.random.default_rng(31)
+    radius, markers = 1.5, 12
+    centres = [np.array([0.4, 6.0, 6.0]), np.array([L - 2.9, 6.5, 6.2]),     # across x = 0
+               np.array([12.0, 0.3, 18.0]), np.array([12.4, L - 2.8, 18.3]),  # across y = 0
+               np.array([18.0, 18.0, 0.2]), np.array([18.2, 18.3, L - 3.0])]  # across z = 0
+    while len(centres) < 40:
+        c = rng.uniform(0.0, L, 3)
+        d = [np.linalg.norm(OC.min_image((c - e)[None, :], shape, False)[0]) for e in centres]
+        if min(d) > 2 * radius + 0.2:
+            centres.append(c)
+    v = synth.fibonacci_sphere(markers)
+    rest = OC.wrap_positions(np.concatenate([c + radius * v for c in centres]), shape, False)
+    B = len(centres)
+    first, count = np.arange(B) * markers, np.full(B, markers)
+    body = OC.RigidBodies.from_positions(rest, first, count, 0.8, 0.3, radius, shape, False)
+    X, _, _ = OC.rigid_frames(body, rest, shape, False)
+    close = 0
+    for b in range(B):
+        for c2 in range(b + 1, B):
+            d = OC.min_image((X[c2] - X[b])[None, :], shape, False)[0]
+            close += np.linalg.norm(d) - 2 * radius < 1.0
+    assert close >= 3                      # the repulsion is exercised
+    M = B * markers
+    parts = dict(pos=rest + 0.02 * rng.standard_normal(rest.shape),
+                 vel=0.003 * rng.standard_normal((M, 3)), mass=0.7,
+                 rigid=dict(first=first, count=count, radius=radius, k=0.8, repulsion_k=0.3,
+                            ref=body.ref))
+    fbar0 = synth.random_populations(shape, seed=5, amp=1e-3)
+    box, sm = make_pair(shape, fbar0, tau=0.7, storage="f64", kind="mebf", stencil="trilinear",
+                        parts=parts)
+    for _ in range(3):
+        sm.step()
+    box.step(3)
+    pos, vel, _ = box.get_particles()
+    assert np.abs(OC.min_image(pos - sm.parts.pos, shape, False)).max() < 1e-11
+    assert np.abs(vel - sm.parts.vel).max() < 1e-11
