@@ -31,7 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "coupled D3Q19 MLUPS & % of HBM peak; ensemble jobs/s with p50/p99 latency"
-WORKLOAD = "cfg2_mrt_chains_256"
+WORKLOAD = "mrt_bead_chains_256"
 LB_KERNEL_SOURCES = ["paper_1406_2211_gb300/csrc/lb_kernels.cu",
                      "paper_1406_2211_gb300/csrc/lb_device.cuh",
                      "paper_1406_2211_gb300/csrc/lbc_common.cuh"]
@@ -307,7 +307,7 @@ def other_workload_boxes(name, storage):
     from paper_1406_2211_gb300 import lbc
     c = synth.config(name)
     nx, ny, nz = c["box"]
-    if name.startswith("cfg3"):
+    if name.startswith("ibm_shells"):
         pos, edges, r0 = synth.shells(c["nshells"], c["radius"], c["box"], c["seed"],
                                       c["subdivisions"])
         lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"],
@@ -335,8 +335,8 @@ def other_workload_boxes(name, storage):
     return box, nx * ny * nz, desc
 
 
-OTHER_WORKLOADS = (("cfg3_ibm_shells_192", ("f32", "bf16dev")),
-                   ("cfg4_mebf_spheres_128", ("f32",)))
+OTHER_WORKLOADS = (("ibm_shells_192", ("f32", "bf16dev")),
+                   ("mebf_rigid_spheres_128", ("f32",)))
 
 
 def run_other_workloads(args, peak, only=None):

@@ -210,12 +210,12 @@ def ensemble_jobs(njobs, seed, edge_range=(32, 128), particles_range=(1, 5000),
 # Parameter presets of the five benchmark workloads.  Readings of the
 # unspecified items are documented next to them.
 CONFIGS = {
-    "cfg1_fc_point_32": dict(
+    "fc_point_particle_32": dict(
         box=(32, 32, 32), collision="bgk", tau=0.8, storage="f64", rho0=1.0,
         kind="fc", gamma=1.0, mass=1.0, stencil="trilinear",
         particle=(16.3, 16.7, 16.1), velocity=(0.01, 0.0, 0.0), steps=1000,
         orders=(2, 1)),
-    "cfg2_mrt_chains_256": dict(
+    "mrt_bead_chains_256": dict(
         box=(256, 256, 256), collision="mrt", tau=1.0, storage="f32",
         rho0=1.0, kind="fc", gamma=5.0, mass=1.0, stencil="trilinear",
         nchains=2000, beads=50, bond_k=10.0, bond_r0=1.0,
@@ -225,13 +225,13 @@ CONFIGS = {
         # once beads share stencil nodes, and with Eq. [multistep] at n = 2
         # for the full 2000 chains: Eq. [multistep] with n = 4 (dt = h/8)
         substeps=4, mode="inside"),
-    "cfg3_ibm_shells_192": dict(
+    "ibm_shells_192": dict(
         box=(192, 192, 192), collision="bgk", tau=1.0, storage="f32",
         rho0=1.0, kind="ibm", stencil="peskin4", nshells=64, radius=8.0,
         subdivisions=3, spring_k=0.05, walls=True,
         wall_velocity=((-0.05, 0.0, 0.0), (0.05, 0.0, 0.0)), seed=12345,
         steps=2000),
-    "cfg4_mebf_spheres_128": dict(
+    "mebf_rigid_spheres_128": dict(
         box=(128, 128, 128), collision="bgk", tau=0.7, storage="f32",
         rho0=1.0, kind="mebf", stencil="peskin4", nspheres=500, radius=4.5,
         markers=400, seed=12345, steps=5000,
@@ -239,7 +239,7 @@ CONFIGS = {
         # rho0 (4/3) pi R^3 / markers tethered to the best-fit rigid frame
         # (stiffness rigid_k), soft repulsion below a one-unit gap
         rigid_k=1.0, repulsion_k=0.1),
-    "cfg5_ensemble": dict(njobs=2000, seed=12345, collision="bgk", tau=0.8,
+    "serving_ensemble": dict(njobs=2000, seed=12345, collision="bgk", tau=0.8,
                           kind="fc", mass=1.0, stencil="trilinear"),
 }
 

@@ -131,12 +131,12 @@ def test_spreading_is_deterministic():
         assert np.array_equal(outs[0][1][k], outs[1][1][k])
 
 
-def test_cfg1_point_particle_32_fp64():
+def test_point_particle_32_fp64():
     """32^3 FP64 BGK tau = 0.8, one particle with force coupling gamma = m = 1,
     trilinear, v0 = (0.01, 0, 0): second- and first-order schemes against the
     oracle, and conservation of m v0 in the periodic box."""
     require_cuda()
-    c = synth.config("cfg1_fc_point_32")
+    c = synth.config("fc_point_particle_32")
     nx, ny, nz = c["box"]
     shape = (nz, ny, nx)
     from oracle import lattice as OLat
@@ -158,14 +158,14 @@ def test_cfg1_point_particle_32_fp64():
         box.close()
 
 
-def test_cfg2_reduced_mrt_chains():
+def test_reduced_mrt_bead_chains():
     """The 256^3 chain workload at 1/4 size: 64^3 MRT FP32, bead chains with
     k = 10 bonds, force coupling gamma = 5, body force 1e-6, the multiple
     time-step split of Sec. 6 (Eq. [multistep]) with n = 2.  FP32 storage and
     FP32 interpolation/spreading: 1e-6 on positions, 1e-5 relative L2 on
     velocities."""
     require_cuda()
-    c = synth.config("cfg2_mrt_chains_256", scale=4)
+    c = synth.config("mrt_bead_chains_256", scale=4)
     nx, ny, nz = c["box"]
     shape = (nz, ny, nx)
     pos, bonds = synth.bead_chains(c["nchains"], c["beads"], c["box"], c["bond_r0"],

@@ -75,7 +75,7 @@ def test_rigid_bodies_momentum_budget():
 
 def test_rigid_spheres_reduced_fp32():
     require_cuda()
-    c = synth.config("cfg4_mebf_spheres_128", scale=4)
+    c = synth.config("mebf_rigid_spheres_128", scale=4)
     nx, ny, nz = c["box"]
     shape = (nz, ny, nx)
     pos, first, count = synth.rigid_spheres(c["nspheres"], c["radius"], c["markers"], c["box"],

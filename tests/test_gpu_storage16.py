@@ -35,7 +35,7 @@ def _periodic_delta(a, b, period):
 
 
 def _shell_case():
-    c = synth.config("cfg3_ibm_shells_192", scale=4)
+    c = synth.config("ibm_shells_192", scale=4)
     nx, ny, nz = c["box"]
     shape = (nz, ny, nx)
     pos, edges, r0 = synth.shells(c["nshells"], c["radius"], c["box"], c["seed"],
