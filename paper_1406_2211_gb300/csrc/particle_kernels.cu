@@ -278,13 +278,17 @@ __device__ inline void block_sum(double (&v)[NV], double (*sh)[FRAME_THREADS]) {
 }
 
 // One block per body: the markers at their pre-drifted positions r1 (the
-// drift's own formula), unwrapped around the first marker; X = their mean,
-// R = polar factor of A = sum (y - X) q^T by the scaled Newton iteration
+// drift's own formula), unwrapped around the first marker r0 as
+// y = r0 + d, d = min_image(r1 - r0); X = their mean, R = polar factor of
+// A = sum (y - X) q^T by the scaled Newton iteration
 // R <- (g R + (g R)^-T) / 2, g = |det R|^(-1/3) (converges to the
-// orthogonal factor, a proper rotation while det A > 0).
+// orthogonal factor, a proper rotation while det A > 0).  One pass over the
+// markers: with m = mean(d), X = r0 + m and A = sum d q^T - m (sum q)^T
+// (the offsets d are below two radii, so no large coordinate enters the
+// sums).
 __global__ void __launch_bounds__(FRAME_THREADS)
 rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
-  __shared__ double sh[9][FRAME_THREADS];
+  __shared__ double sh[15][FRAME_THREADS];
   const RigidArgs& rg = d.rigid;
   const int b = blockIdx.x;
   const long long M = p.M;
@@ -297,31 +301,38 @@ rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
     const double v = d.vel_in[c * M + f];
     r0[c] = (d.pos_in[c * M + f] + d.dt_pre0 * v) + d.dt_pre * v;
   }
-  auto y_of = [&](long long i, double (&y)[3]) {
+  // sums: d (3), q (3), d q^T (9)
+  double acc[15];
+#pragma unroll
+  for (int v = 0; v < 15; ++v) acc[v] = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
+    const long long i = f + k;
+    double dv[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double v = d.vel_in[c * M + i];
       const double r1 = (d.pos_in[c * M + i] + d.dt_pre0 * v) + d.dt_pre * v;
-      y[c] = r0[c] + min_image(r1 - r0[c], n3[c], per[c]);
+      dv[c] = min_image(r1 - r0[c], n3[c], per[c]);
     }
-  };
-  double s3[3] = {0.0, 0.0, 0.0};
-  for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
-    double y[3];
-    y_of(f + k, y);
-    for (int c = 0; c < 3; ++c) s3[c] += y[c];
-  }
-  block_sum<3>(s3, sh);
-  const double X[3] = {s3[0] / cnt, s3[1] / cnt, s3[2] / cnt};
-  double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
-    const long long i = f + k;
-    double y[3];
-    y_of(i, y);
     const double q[3] = {rg.ref[i], rg.ref[M + i], rg.ref[2 * M + i]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] += dv[c];
+      acc[3 + c] += q[c];
+    }
+#pragma unroll
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) A[3 * r + c] += (y[r] - X[r]) * q[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[6 + 3 * r + c] += dv[r] * q[c];
   }
-  block_sum<9>(A, sh);
+  block_sum<15>(acc, sh);
+  const double m[3] = {acc[0] / cnt, acc[1] / cnt, acc[2] / cnt};
+  const double X[3] = {r0[0] + m[0], r0[1] + m[1], r0[2] + m[2]};
+  double A[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[3 * r + c] = acc[6 + 3 * r + c] - m[r] * acc[3 + c];
   if (threadIdx.x == 0) {
     double R[9], Ri[9];
     for (int k = 0; k < 9; ++k) R[k] = A[k];
