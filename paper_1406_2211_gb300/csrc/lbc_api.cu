@@ -407,14 +407,22 @@ struct Plan {
     if (!on()) return;
     const int kb = key_bits(b->L.ntiles);
     int* need = need_flag();
-    launch_sort(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
-                b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->uptr(b->L.off_key[1]),
-                b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), need, s);
     int* mcount = b->mom_on ? b->iptr(b->L.off_mcount) : nullptr;
-    launch_bins(b->L.ntiles, b->M, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
-                b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home), need,
-                changed_flag(), mcount, s);
-    if (b->M > 0) n += 3 * sort_passes(kb) + 2;
+    if (b->M <= small_sort_max()) {
+      launch_small_sort_bins(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
+                             b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->L.ntiles,
+                             b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home),
+                             need, changed_flag(), mcount, s);
+      if (b->M > 0) ++n;
+    } else {
+      launch_sort(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
+                  b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->uptr(b->L.off_key[1]),
+                  b->uptr(b->L.off_idx[1]), b->iptr(b->L.off_hist), need, s);
+      launch_bins(b->L.ntiles, b->M, b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]),
+                  b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home), need,
+                  changed_flag(), mcount, s);
+      if (b->M > 0) n += 3 * sort_passes(kb) + 2;
+    }
     if (mcount) {
       // the bricks the node-moment pass fills while these bins hold
       launch_moment_bricks(b->L.g, b->iptr(b->L.off_tb), b->iptr(b->L.off_te), need,
@@ -1482,6 +1490,7 @@ struct lbc_batch {
   std::vector<cudaStream_t> streams;     // one per slot
   std::vector<cudaEvent_t> events;       // one per slot
   cudaEvent_t fork[2];
+  cudaEvent_t done_ev;     // recorded after each advance's work (any stream)
   cudaGraphExec_t graph[2];
   cudaGraph_t tgraph[2];
   cudaStream_t graph_stream[2];
@@ -1622,9 +1631,15 @@ lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
       return LBC_ERR_STATE;
     }
   }
-  // the box tables the captured launches read
-  CK(cudaMemcpy(region0, host[0].data(), host[0].size() * sizeof(BoxEntry), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(region1, host[1].data(), host[1].size() * sizeof(BoxEntry), cudaMemcpyHostToDevice));
+  // the box tables the captured launches read, written after the batch's
+  // earlier work (on whichever stream it ran) and before this graph's
+  // launches, without blocking the host (asynchronous copies from pageable
+  // memory are staged before the call returns)
+  CK(cudaStreamWaitEvent(s, B->done_ev, 0));
+  CK(cudaMemcpyAsync(region0, host[0].data(), host[0].size() * sizeof(BoxEntry),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(region1, host[1].data(), host[1].size() * sizeof(BoxEntry),
+                     cudaMemcpyHostToDevice, s));
   cudaGraphExec_t exec;
   e = cudaGraphInstantiate(&exec, graph, 0);
   if (e != cudaSuccess) {
@@ -1677,8 +1692,10 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
     B->graph_stream[k] = nullptr;
     B->fork[k] = nullptr;
   }
+  B->done_ev = nullptr;
   bool ok = cudaEventCreateWithFlags(&B->fork[0], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&B->fork[1], cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&B->fork[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming) == cudaSuccess;
   B->streams.assign(max_boxes, nullptr);
   B->events.assign(max_boxes, nullptr);
   for (int j = 0; ok && j < max_boxes; ++j)
@@ -1744,9 +1761,9 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
       CK(cudaGraphLaunch(B->graph[par], s));
       done += 2;
     } else {
-      // eager step: the table region is rewritten only after the previous
-      // eager step's launches are done
-      CK(cudaStreamSynchronize(s));
+      // eager step: its table region is rewritten after the batch's earlier
+      // work (the event), without the host waiting for the device
+      CK(cudaStreamWaitEvent(s, B->done_ev, 0));
       BoxEntry* region = B->tables + (size_t)4 * B->max_boxes;
       int64_t l = 0;
       lbc_status st = batch_step(B, s, region, host, true, &l);
@@ -1756,6 +1773,7 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
       done += 1;
     }
   }
+  CK(cudaEventRecord(B->done_ev, s));
   for (auto& m : B->members) m.remaining -= k;
   for (int j = (int)B->members.size() - 1; j >= 0; --j) {
     if (B->members[j].remaining > 0) continue;
@@ -1778,6 +1796,7 @@ lbc_status lbc_batch_destroy(lbc_batch* B) {
   batch_reset_graphs(B);
   for (int k = 0; k < 2; ++k)
     if (B->fork[k]) cudaEventDestroy(B->fork[k]);
+  if (B->done_ev) cudaEventDestroy(B->done_ev);
   for (cudaStream_t st : B->streams)
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t ev : B->events)

@@ -151,6 +151,14 @@ int sort_passes(int key_bits);
 void launch_sort(long long M, int key_bits, const uint32_t* kin, const uint32_t* vin, uint32_t* ka,
                  uint32_t* va, uint32_t* kb, uint32_t* vb, int* hist, const int* need,
                  cudaStream_t s);
+// up to this many markers the sort and the bins run as one single-block
+// launch (launch_small_sort_bins), with the same results
+constexpr long long SMALL_SORT_MAX = 8192;
+long long small_sort_max();
+void launch_small_sort_bins(long long M, int key_bits, const uint32_t* kin, const uint32_t* vin,
+                            uint32_t* ka, uint32_t* va, int ntiles, int* tile_begin,
+                            int* tile_end, uint32_t* home, const int* need, int* changed,
+                            int* brick_count, cudaStream_t s);
 // tile ranges, home tiles and the "bins changed" flag after a sort (same
 // condition); zeroes *brick_count too when it is not null
 void launch_bins(int ntiles, long long M, const uint32_t* sorted_keys, const uint32_t* idx,

@@ -618,6 +618,109 @@ void launch_bins(int ntiles, long long M, const uint32_t* keys, const uint32_t* 
                                                                      changed);
 }
 
+// Few markers: the whole re-binning in one block and one launch (a no-op
+// while no marker left its bin), so a small box's step carries one gated
+// launch instead of the radix passes and the bins.  A stable LSD sort of the
+// (key, index) pairs by one key bit per pass in shared memory (each thread
+// owns a contiguous run of elements; a block-wide prefix sum of its zero
+// bits places them), which gives the same order as any stable sort by key,
+// then the tile ranges, home tiles and flags as bins_kernel writes them.
+constexpr int SMALL_SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_SORT_THREADS)
+small_sort_bins_kernel(int n, int key_bits, const uint32_t* __restrict__ kin,
+                       const uint32_t* __restrict__ vin, uint32_t* __restrict__ ka,
+                       uint32_t* __restrict__ va, int ntiles, int* __restrict__ tb,
+                       int* __restrict__ te, uint32_t* __restrict__ home, const int* need,
+                       int* changed, int* brick_count) {
+  if (skip(need)) return;
+  extern __shared__ uint32_t ssort[];
+  __shared__ int wsum[SMALL_SORT_THREADS / 32];
+  const unsigned full = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  constexpr int NW = SMALL_SORT_THREADS / 32;
+  uint32_t* k0 = ssort;
+  uint32_t* v0 = ssort + n;
+  uint32_t* k1 = ssort + 2 * n;
+  uint32_t* v1 = ssort + 3 * n;
+  for (int i = t; i < n; i += SMALL_SORT_THREADS) {
+    k0[i] = kin[i];
+    v0[i] = vin[i];
+  }
+  for (int q = t; q < ntiles; q += SMALL_SORT_THREADS) {
+    tb[q] = 0;
+    te[q] = 0;
+  }
+  __syncthreads();
+  const int per = (n + SMALL_SORT_THREADS - 1) / SMALL_SORT_THREADS;
+  const int lo = min(t * per, n), hi = min(lo + per, n);
+  for (int bit = 0; bit < key_bits; ++bit) {
+    int zeros = 0;
+    for (int i = lo; i < hi; ++i) zeros += ((k0[i] >> bit) & 1u) == 0u;
+    int incl = zeros;                  // inclusive scan of the zeros over the block
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(full, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int sw = wsum[lane];
+#pragma unroll
+      for (int off = 1; off < NW; off <<= 1) {
+        const int v = __shfl_up_sync(full, sw, off);
+        if (lane >= off) sw += v;
+      }
+      wsum[lane] = sw;
+    }
+    __syncthreads();
+    const int zeros_before = incl - zeros + (w > 0 ? wsum[w - 1] : 0);
+    const int total_zeros = wsum[NW - 1];
+    int z = zeros_before, o = total_zeros + (lo - zeros_before);
+    for (int i = lo; i < hi; ++i) {
+      const uint32_t key = k0[i];
+      const int dst = ((key >> bit) & 1u) ? o++ : z++;
+      k1[dst] = key;
+      v1[dst] = v0[i];
+    }
+    __syncthreads();
+    uint32_t* tk = k0; k0 = k1; k1 = tk;
+    uint32_t* tv = v0; v0 = v1; v1 = tv;
+  }
+  for (int i = t; i < n; i += SMALL_SORT_THREADS) {
+    const uint32_t key = k0[i];
+    ka[i] = key;
+    va[i] = v0[i];
+    if (i == 0 || k0[i - 1] != key) tb[key] = i;
+    if (i == n - 1 || k0[i + 1] != key) te[key] = i + 1;
+    home[v0[i]] = key;
+  }
+  if (t == 0) {
+    if (changed) *changed = 1;
+    if (brick_count) *brick_count = 0;
+  }
+}
+
+long long small_sort_max() { return SMALL_SORT_MAX; }
+
+void launch_small_sort_bins(long long M, int key_bits, const uint32_t* kin, const uint32_t* vin,
+                            uint32_t* ka, uint32_t* va, int ntiles, int* tb, int* te,
+                            uint32_t* home, const int* need, int* changed, int* brick_count,
+                            cudaStream_t s) {
+  if (M <= 0) return;
+  static bool attr = false;
+  const size_t smem = (size_t)16 * (size_t)M;
+  if (!attr) {
+    cudaFuncSetAttribute(small_sort_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(16 * SMALL_SORT_MAX));
+    attr = true;
+  }
+  small_sort_bins_kernel<<<1, SMALL_SORT_THREADS, smem, s>>>((int)M, key_bits, kin, vin, ka, va,
+                                                             ntiles, tb, te, home, need, changed,
+                                                             brick_count);
+}
+
 // ------------------------------------------------------------ gather + couple
 // j and 1 / rho at node (x, y, z)
 template <typename S, bool WALLS>

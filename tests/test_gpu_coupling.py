@@ -214,3 +214,28 @@ def test_fast_markers_are_rebinned_in_graph_replays():
     assert box.status() == 0
     disp = np.abs(OC.min_image(sm.parts.pos - OC.wrap_positions(pos, shape, False), shape, False))
     assert disp.max() > 8.0                     # markers crossed several bins
+
+
+@pytest.mark.parametrize("M", [8000, 9000])
+def test_single_block_and_multi_pass_sorts(M):
+    """Up to 8192 markers the re-binning runs as one single-block launch,
+    above it as radix passes plus the bins: both against the oracle, with
+    markers fast enough to leave their bins (re-sorts in graph replays)."""
+    require_cuda()
+    shape = (20, 20, 24)
+    rng = np.random.default_rng(M)
+    pos = rng.uniform(0.0, 1.0, (M, 3)) * [24, 20, 20]
+    parts = dict(pos=pos, vel=0.2 * rng.standard_normal((M, 3)), mass=2.0)
+    fbar0 = synth.random_populations(shape, seed=2, amp=1e-3)
+    box, sm = make_pair(shape, fbar0, tau=0.8, storage="f64", kind="fc", order=2,
+                        stencil="trilinear", gamma=1.5, parts=parts)
+    for nsteps in (1, 2, 4):
+        box.step(nsteps)
+        for _ in range(nsteps):
+            sm.step()
+    pos_g, vel_g, _ = box.get_particles()
+    assert np.abs(OC.min_image(pos_g - sm.parts.pos, shape, False)).max() < 1e-11
+    assert np.abs(vel_g - sm.parts.vel).max() < 1e-11
+    assert box.status() == 0
+    tile0 = np.floor(OC.wrap_positions(pos, shape, False) / 4.0)
+    assert (np.floor(pos_g / 4.0) != tile0).any(axis=1).sum() > 100   # re-binned markers
