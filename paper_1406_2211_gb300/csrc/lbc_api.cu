@@ -1483,6 +1483,7 @@ struct lbc_batch {
   struct Member {
     lbc_box* box;
     int64_t remaining;
+    bool stepped;    // has taken a step in this batch (its first one eagerly)
   };
   int max_boxes;
   BoxEntry* tables;                 // 5 regions of max_boxes entries (device)
@@ -1662,6 +1663,11 @@ void batch_drop(lbc_batch* B, int j) {
   B->members[j].box->batch = nullptr;
   B->members.erase(B->members.begin() + j);
   batch_reset_graphs(B);
+  // members that have all stepped here can be captured at once (a new box
+  // takes its first step, which sorts its markers, eagerly)
+  bool all = !B->members.empty();
+  for (const auto& m : B->members) all = all && m.stepped;
+  B->steady = all;
 }
 
 }  // namespace
@@ -1715,7 +1721,7 @@ lbc_status lbc_batch_add(lbc_batch* B, lbc_box* b, int64_t steps) {
   if (b->batch != nullptr || b->timing_cap > 0) return LBC_ERR_STATE;
   if ((int)B->members.size() >= B->max_boxes) return LBC_ERR_OOM;
   if (b->status != LBC_OK) return b->status;
-  B->members.push_back({b, steps});
+  B->members.push_back({b, steps, false});
   b->batch = B;
   batch_reset_graphs(B);
   return LBC_OK;
@@ -1770,6 +1776,7 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
       if (st != LBC_OK) return st;
       B->launches = l;
       B->steady = true;
+      for (auto& m : B->members) m.stepped = true;
       done += 1;
     }
   }
