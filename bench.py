@@ -262,7 +262,8 @@ def run_gpu(args, rank, world, local_rank):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
         h2d = hpos.nbytes + hvel.nbytes + M * 8 + bonds.nbytes + 2 * B * 8
-        d2h = rpos.nbytes + rvel.nbytes + M * 24 + 4 * 8
+        # F^h comes back in the compute type (FP32 unless the storage is FP64)
+        d2h = rpos.nbytes + rvel.nbytes + M * (24 if c["storage"] == "f64" else 12) + 4 * 8
         e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "scope": "lbc_box_set_particles (host arrays) + lbc_box_step + "
