@@ -163,6 +163,11 @@ def test_default_follows_the_node_count():
         multi.set_option(lbc.LBC_OPT_NODE_MOMENTS, 1)
     sparse.set_option(lbc.LBC_OPT_NODE_MOMENTS, 1)
     assert sparse.get_option(lbc.LBC_OPT_NODE_MOMENTS) == 1
+    for option, bad in ((lbc.LBC_OPT_NODE_MOMENTS, 2), (lbc.LBC_OPT_GATHER_LANES, 3),
+                        (lbc.LBC_OPT_GATHER_LANES, -1)):
+        with pytest.raises(lbc.LBCError):
+            sparse.set_option(option, bad)
+    assert sparse.get_option(lbc.LBC_OPT_GATHER_LANES) == 0     # automatic by default
 
 
 def test_batch_member_with_field_equals_alone():
