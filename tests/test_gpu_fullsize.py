@@ -1,0 +1,96 @@
+"""Parity at the full size of the 256^3 bead-chain workload, in the launch
+configuration the benchmark times (MRT with fully relaxed ghosts, FP32
+deviations, the force-field variant of the fused LB kernel, autotuned block
+shape).
+
+* One LB step checked on sampled cells: the step is local (a cell's new
+  populations come from the collisions at its 19 upstream neighbours), so the
+  oracle's recombined step applied to the 3 x 3 x 3 neighbourhood of a cell,
+  taken from the GPU's own input state, gives the exact result at its centre.
+  Bound: FP32 arithmetic on deviations of order 1e-3 w_i, so 1e-7 absolute
+  (a dropped or mis-signed term is of order 1e-6 to 1e-4).
+* The coupled step over 20 steps: total mass conserved and the fluid plus
+  particle momentum growing by exactly t g N (Eq. [fc-splitting] conserves
+  momentum; the body force g acts on N cells), at FP32 roundoff.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lb as OL
+from tests.gpu_helpers import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+NAME = "mrt_bead_chains_256"
+
+
+def _lattice(lbc, c):
+    nx, ny, nz = c["box"]
+    return lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                            body_force=c["body_force"], storage=c["storage"])
+
+
+def _coupling(lbc, c):
+    return lbc.coupling_desc(c["kind"], 2, c["stencil"], gamma=c["gamma"], split=c["mode"],
+                             substeps=c["substeps"])
+
+
+def test_lb_step_256_on_sampled_cells():
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    c = synth.config(NAME)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    # force fields allocated, no particle set: the step is the LB step with
+    # the pending force F_a (h/2) and the body force (h)
+    box = lbc.Box(_lattice(lbc, c), _coupling(lbc, c), max_particles=1)
+    box.autotune()
+    box.set_populations(synth.random_populations(shape, seed=44, amp=1e-3))
+    f0 = box.get_populations()                  # the stored FP32 state, exactly
+    rng = np.random.default_rng(45)
+    Fa = 1e-4 * rng.standard_normal((3,) + shape)
+    box.set_pending_force(Fa)
+    box.step(1)
+    f1 = box.get_populations()
+    box.close()
+    p = OL.LBParams(collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                    body_force=c["body_force"])
+    cells = rng.integers(0, [nz, ny, nx], size=(400, 3))
+    corners = [[z, y, x] for z in (0, nz - 1) for y in (0, ny - 1) for x in (0, nx - 1)]
+    cells[:len(corners)] = corners                # periodic wrap on every face
+    err = 0.0
+    for z, y, x in cells:
+        iz = (z + np.arange(-1, 2)) % nz
+        iy = (y + np.arange(-1, 2)) % ny
+        ix = (x + np.arange(-1, 2)) % nx
+        loc = f0[:, iz][:, :, iy][:, :, :, ix]
+        Floc = Fa[:, iz][:, :, iy][:, :, :, ix]
+        out = OL.step_recombined(loc, Floc, None, p)[:, 1, 1, 1]
+        err = max(err, float(np.abs(out - f1[:, z, y, x]).max()))
+    assert err < 1e-7, err
+
+
+def test_bead_chain_workload_256_mass_and_momentum():
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    c = synth.config(NAME)
+    nx, ny, nz = c["box"]
+    pos, bonds = synth.bead_chains(c["nchains"], c["beads"], c["box"], c["bond_r0"],
+                                   seed=c["seed"])
+    box = lbc.Box(_lattice(lbc, c), _coupling(lbc, c), max_particles=len(pos),
+                  max_bonds=len(bonds))
+    box.autotune()
+    box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
+    box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
+                      bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+    m0, P0, st0 = box.invariants()
+    steps = 20
+    box.step(steps)
+    m1, P1, st1 = box.invariants()
+    box.close()
+    assert st0 == 0 and st1 == 0
+    N = nx * ny * nz
+    assert abs(m1 - m0) <= 1e-9 * m0
+    expect = steps * np.asarray(c["body_force"]) * N
+    assert np.abs(P1 - P0 - expect).max() <= 1e-3 * np.abs(expect).max(), (P1 - P0, expect)
