@@ -94,3 +94,59 @@ def test_bead_chain_workload_256_mass_and_momentum():
     assert abs(m1 - m0) <= 1e-9 * m0
     expect = steps * np.asarray(c["body_force"]) * N
     assert np.abs(P1 - P0 - expect).max() <= 1e-3 * np.abs(expect).max(), (P1 - P0, expect)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16dev"])
+def test_lb_step_192_walls_on_sampled_cells(storage):
+    """The 192^3 shell configuration's LB variant (BGK, moving walls with
+    halfway bounce-back in z, force fields): sampled interior and wall cells
+    against the oracle.  A wall cell's neighbourhood is the two layers next
+    to the wall, streamed with the oracle's walls (the other face of that
+    two-layer box is not read).  BF16 stores each scaled deviation rounded
+    stochastically to one of its two neighbours in BF16, so the bound is
+    one BF16 spacing (at most 2^-6 of the exact value's magnitude) plus the
+    FP32 bound."""
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    from oracle import lattice as OLat
+    c = synth.config("ibm_shells_192")
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    uw = c["wall_velocity"]
+    lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                           walls=True, wall_velocity=uw, storage=storage)
+    box = lbc.Box(lat, lbc.coupling_desc("ibm", 2, c["stencil"]), max_particles=1)
+    box.autotune()
+    box.set_populations(synth.random_populations(shape, seed=46, amp=1e-3))
+    f0 = box.get_populations()
+    rng = np.random.default_rng(47)
+    Fa = 1e-4 * rng.standard_normal((3,) + shape)
+    box.set_pending_force(Fa)
+    box.step(1)
+    f1 = box.get_populations()
+    box.close()
+    cells = rng.integers(0, [nz, ny, nx], size=(300, 3))
+    cells[:100, 0] = 0                             # bottom wall layer
+    cells[100:200, 0] = nz - 1                     # top wall layer
+    w0 = (OLat.W * c["rho0"]).reshape(-1)
+    worst = 0.0
+    for z, y, x in cells:
+        iy = (y + np.arange(-1, 2)) % ny
+        ix = (x + np.arange(-1, 2)) % nx
+        if z == 0:
+            iz, zc, walls = np.array([0, 1]), 0, True
+        elif z == nz - 1:
+            iz, zc, walls = np.array([nz - 2, nz - 1]), 1, True
+        else:
+            iz, zc, walls = z + np.arange(-1, 2), 1, False
+        pl = OL.LBParams(collision=c["collision"], tau=c["tau"], rho0=c["rho0"], walls=walls,
+                         u_bot=uw[0], u_top=uw[1]) if walls else OL.LBParams(
+                             collision=c["collision"], tau=c["tau"], rho0=c["rho0"])
+        loc = f0[:, iz][:, :, iy][:, :, :, ix]
+        Floc = Fa[:, iz][:, :, iy][:, :, :, ix]
+        out = OL.step_recombined(loc, Floc, None, pl)[:, zc, 1, 1]
+        got = f1[:, z, y, x]
+        # one BF16 spacing: 2^-7 of the value, 2^-6 of the value below it
+        tol = 1e-7 + (2.0 ** -6 * np.abs(out - w0) if storage == "bf16dev" else 0.0)
+        worst = max(worst, float((np.abs(out - got) / tol).max()))
+    assert worst <= 1.0, worst
