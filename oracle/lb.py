@@ -27,7 +27,7 @@ Two step forms, checked against each other in the tests:
        shifts the equilibrium velocity (see force_half_step); it needs no
        square root of (1 - Lambda), so it also holds for tau < 1.
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
   * tau is the standard lattice relaxation time, lambda = 1/tau for BGK
     (full step), nu = (tau - 1/2)/3.  The paper's continuous tau of
     Eq. [BGKlambda] is tau_paper = tau - 1/2 to O(h^2).
