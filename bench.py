@@ -147,6 +147,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+def max_over_ranks(ms, world, device):
+    """The job's time: the slowest rank's, the same on every rank (replicas
+    share no data; this is the only collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells, steps, world, ms):
+    """Lattice updates of all ranks' replicas over the job's time."""
+    return world * cells * steps / (ms * 1e-3) / 1e6
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -203,11 +219,8 @@ def run_gpu(args, rank, world, local_rank):
         box.close()
         del box
         torch.cuda.empty_cache()
-        t = torch.tensor([r["ms"]], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        r["ms_max"] = float(t.item())
-        r["value"] = world * cells * steps / (r["ms_max"] * 1e-3) / 1e6
+        r["ms_max"] = max_over_ranks(r["ms"], world, "cuda")
+        r["value"] = whole_job_mlups(cells, steps, world, r["ms_max"])
         r["lb_avg_ms"] = r["lb_ms"] / r["lb_n"]
         r["achieved"] = BYTES_PER_CELL[storage] * cells / (r["lb_avg_ms"] * 1e-3) / 1e9
         return r
@@ -257,14 +270,11 @@ def run_gpu(args, rank, world, local_rank):
         _, _, st2 = box2.invariants()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+        t_e2e = max_over_ranks(t_e2e, world, "cuda")
         h2d = hpos.nbytes + hvel.nbytes + M * 8 + bonds.nbytes + 2 * B * 8
         # F^h comes back in the compute type (FP32 unless the storage is FP64)
         d2h = rpos.nbytes + rvel.nbytes + M * (24 if c["storage"] == "f64" else 12) + 4 * 8
-        e2e = {"value": world * cells * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+        e2e = {"value": whole_job_mlups(cells, args.steps, world, t_e2e * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "scope": "lbc_box_set_particles (host arrays) + lbc_box_step + "
                         "lbc_box_get_particles + lbc_box_invariants"}
