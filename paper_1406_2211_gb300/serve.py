@@ -127,9 +127,11 @@ def summary(jobs, elapsed):
 
 class BoxFactory:
     """Builds library boxes for ensemble jobs: cubic periodic box of edge
-    spec["edge"], BGK tau, force-coupled point particles (trilinear,
-    friction spec["gamma"], mass 1) at spec["pos"] with velocities
-    spec["vel"], storage spec["storage"]."""
+    spec["edge"] and storage spec["storage"], with particles at spec["pos"].
+    Optional keys (defaults in brackets): "collision" ["bgk"], "tau" [the
+    factory's], "kind" ["fc"; "ebf", "mebf", "ibm"], "stencil"
+    ["trilinear"; "peskin4", "peskin3"], "gamma" [1.0], "mass" [1.0],
+    "vel" [zero]; markers of an "ibm" job carry neither mass nor velocity."""
 
     def __init__(self, tau=0.8, rho0=1.0, stream=None):
         from . import lbc
@@ -141,9 +143,11 @@ class BoxFactory:
     def _descs(self, job):
         s = job.spec
         L = int(s["edge"])
-        lat = self.lbc.lattice_desc(L, L, L, collision="bgk", tau=self.tau, rho0=self.rho0,
+        lat = self.lbc.lattice_desc(L, L, L, collision=s.get("collision", "bgk"),
+                                    tau=float(s.get("tau", self.tau)), rho0=self.rho0,
                                     storage=s["storage"])
-        cpl = self.lbc.coupling_desc("fc", 2, "trilinear", gamma=float(s["gamma"]))
+        cpl = self.lbc.coupling_desc(s.get("kind", "fc"), 2, s.get("stencil", "trilinear"),
+                                     gamma=float(s.get("gamma", 1.0)))
         return lat, cpl, len(s["pos"])
 
     def bytes(self, job):
@@ -159,7 +163,11 @@ class BoxFactory:
         lat, cpl, M = self._descs(job)
         box = self.lbc.Box(lat, cpl, max_particles=M, stream=self.stream)
         box.init_equilibrium(self.rho0, (0.0, 0.0, 0.0))
-        box.set_particles(job.spec["pos"], vel=job.spec.get("vel"), mass=1.0)
+        s = job.spec
+        if s.get("kind", "fc") == "ibm":
+            box.set_particles(s["pos"])
+        else:
+            box.set_particles(s["pos"], vel=s.get("vel"), mass=float(s.get("mass", 1.0)))
         return box
 
     def result(self, box):

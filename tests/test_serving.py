@@ -147,3 +147,23 @@ def test_summary_statistics():
     assert s["p99_latency_s"] == pytest.approx(np.percentile(lat, 99))
     assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
     assert s["cell_updates"] == sum(j.cells * j.steps for j in jobs)
+
+
+def test_box_factory_descriptors_follow_the_job_spec():
+    """The library factory maps a job's coupling kind, stencil, collision,
+    tau and storage into the box descriptors; its device-memory query is
+    host-only."""
+    from paper_1406_2211_gb300 import lbc
+    from paper_1406_2211_gb300.serve import BoxFactory
+    fac = BoxFactory(tau=0.9)
+    pos = np.zeros((10, 3))
+    plain = Job(0, dict(edge=16, storage="f32", pos=pos), 0.0, 5, 16 ** 3)
+    lat, cpl, M = fac._descs(plain)
+    assert (lat.collision, lat.tau, lat.storage) == (lbc.LBC_BGK, 0.9, lbc.LBC_F32)
+    assert (cpl.kind, cpl.stencil, cpl.gamma, M) == (lbc.LBC_FC, lbc.LBC_TRILINEAR, 1.0, 10)
+    ibm = Job(1, dict(edge=24, storage="bf16dev", pos=pos, kind="ibm", stencil="peskin4",
+                      collision="mrt", tau=1.1), 0.0, 5, 24 ** 3)
+    lat, cpl, M = fac._descs(ibm)
+    assert (lat.collision, lat.tau, lat.storage) == (lbc.LBC_MRT, 1.1, lbc.LBC_BF16_DEV)
+    assert (cpl.kind, cpl.stencil) == (lbc.LBC_IBM, lbc.LBC_PESKIN4)
+    assert fac.bytes(ibm) > fac.bytes(plain) > 16 ** 3 * 2 * 19 * 4
