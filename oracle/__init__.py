@@ -21,6 +21,8 @@ Modules
   coupling  IBM / force coupling / EBF / modified EBF operators (Sec. 5),
             first- and second-order schemes, multiple time steps (Sec. 6)
   sim       a simulation box that strings the operators into time steps
+  fluct     fluctuating MRT collision (Eq. [mrt-fluct]) with a counter-based
+            random number generator; recombined and literal fluctuating steps
 
 Parity pins (what ties each part to the paper rather than to itself) are
 the tests in tests/test_oracle_*.py.  Parts without an independent pin are
