@@ -270,6 +270,23 @@ lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
 /* Current value of an option (LBC_OPT_TIMING: the event pairs reserved). */
 lbc_status lbc_box_get_option(const lbc_box* box, int32_t option, int64_t* value);
 
+/* Thermal fluctuations of the fluid (Sec. 3.2, Eq. [mrt-fluct]): from the
+ * next step on, every LB step kicks the non-equilibrium part of each
+ * non-conserved moment k (in the MRT basis; BGK uses the same form with one
+ * eigenvalue) by sqrt(rho) phi_k r_k, phi_k^2 = mu b_k (1 - gamma_k^2),
+ * mu = k_B T / (a^3 cs2), gamma_k = 1 - lambda_k, r_k standard normal.  (The
+ * paper prints phi_k = sqrt(mu b_k lambda_k^2); the form used keeps the
+ * moments at their equilibrium variance mu rho b_k.)  The r_k come from
+ * Philox4x32-10 with counter (x + nx (y + ny z), step, 0, k / 4) and key
+ * (low, high 32 bits of seed), Box-Muller pairs (cos, sin) of uniforms
+ * (0, 1) and (2, 3) of a block giving r_{4 block} .. r_{4 block + 3}; the
+ * step counter restarts at 0 here and advances once per LB step.
+ * kT = 0 switches the fluctuations off.  Particle (coupling) noise is not
+ * included.  Errors: LBC_ERR_ARG for kT < 0 or non-finite; LBC_ERR_STATE for
+ * a batch member or 16-bit storage with kT > 0 (thermal boxes cannot join a
+ * batch).  Drops the captured step graphs. */
+lbc_status lbc_box_set_thermal(lbc_box* box, double kT, uint64_t seed);
+
 /* Sum of the event-measured durations (ms) of the LB kernel launches timed
  * since the last reset, and their count; waits for the last event.
  * reset != 0 restarts the count. */

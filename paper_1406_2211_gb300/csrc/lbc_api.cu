@@ -73,6 +73,7 @@ struct Layout {
   size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
       off_rb_frep;
   size_t off_red, off_redout;
+  size_t off_thermal;                // step counter of the thermal fluctuations
   int ntiles, maxnt;
   bool has_particles;
   bool use_ncache;
@@ -158,6 +159,7 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
+  L.off_thermal = take(sizeof(unsigned long long));
   L.total = o;
   return L;
 }
@@ -198,6 +200,8 @@ struct lbc_box {
   lbc_batch* batch;    // the batch this box belongs to, or null
   bool mom_on;         // gathers read the node-moment field (LBC_OPT_NODE_MOMENTS)
   int gather_lanes;    // LBC_OPT_GATHER_LANES
+  bool thermal;        // LB steps with thermal fluctuations (lbc_box_set_thermal)
+  FluctArgs fl;        // their amplitudes and Philox key
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
   void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
@@ -335,7 +339,13 @@ struct Plan {
     // graph (external events), not capture-internal dependencies
     const unsigned rf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (e0) cudaEventRecordWithFlags(e0, s, rf);
-    launch_lb_step(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
+    if (b->thermal) {
+      launch_lb_fluct(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, b->fl,
+                      reinterpret_cast<unsigned long long*>(b->arena + b->L.off_thermal), s);
+      ++n;                 // the step counter's advance
+    } else {
+      launch_lb_step(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
+    }
     if (e1) cudaEventRecordWithFlags(e1, s, rf);
     b->cur = 1 - b->cur;
     ++n;
@@ -942,6 +952,8 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->rigid_k = b->rigid_krep = 0.0;
   b->mom_on = L.has_particles && L.has_mom && moments_pay(L, b->cpl, max_particles);
   b->gather_lanes = 0;
+  b->thermal = false;
+  std::memset(&b->fl, 0, sizeof(b->fl));
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -1367,6 +1379,35 @@ lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) 
   return LBC_OK;
 }
 
+lbc_status lbc_box_set_thermal(lbc_box* b, double kT, uint64_t seed) {
+  if (!b || !(kT >= 0.0) || !std::isfinite(kT)) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;
+  const int st = b->lat.storage;
+  if (kT > 0.0 && st != LBC_F32 && st != LBC_F64) return LBC_ERR_STATE;
+  reset_graphs(b);
+  b->thermal = kT > 0.0;
+  std::memset(&b->fl, 0, sizeof(b->fl));
+  if (!b->thermal) return LBC_OK;
+  // eigenvalues 1 - lambda per relaxation group (BGK: one for all)
+  const bool mrt = b->lat.collision == LBC_MRT;
+  double gk[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int q = 1; q < 5; ++q) gk[q] = mrt ? b->lb.gamma_k[q - 1].d : b->lb.gamma_bgk.d;
+  for (int q = 0; q < 5; ++q) b->fl.gk[q] = make_real(gk[q]);
+  const double mu = kT / (1.0 / 3.0);          // k_B T / (a^3 cs2), a = 1
+  for (int k = 4; k < Q; ++k) {
+    const double gam = gk[mrt_group(k)];
+    const double bk = mrt_b(k);
+    b->fl.psi[k] = make_real(std::sqrt(mu * bk * (1.0 - gam * gam)) / bk);
+  }
+  b->fl.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  b->fl.key1 = (uint32_t)(seed >> 32);
+  b->fl.step = reinterpret_cast<const unsigned long long*>(b->arena + b->L.off_thermal);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemset(b->arena + b->L.off_thermal, 0, sizeof(unsigned long long)));
+  CK(cudaDeviceSynchronize());
+  return LBC_OK;
+}
+
 lbc_status lbc_box_lb_timing(lbc_box* b, double* ms_total, int64_t* launches, int32_t reset) {
   if (!b || !ms_total || !launches) return LBC_ERR_ARG;
   double tot = 0.0;
@@ -1718,7 +1759,7 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
 lbc_status lbc_batch_add(lbc_batch* B, lbc_box* b, int64_t steps) {
   if (!B || !b || steps < 1) return LBC_ERR_ARG;
   if (b->L.g.nx > LBC_BATCH_MAX_NX) return LBC_ERR_ARG;
-  if (b->batch != nullptr || b->timing_cap > 0) return LBC_ERR_STATE;
+  if (b->batch != nullptr || b->timing_cap > 0 || b->thermal) return LBC_ERR_STATE;
   if ((int)B->members.size() >= B->max_boxes) return LBC_ERR_OOM;
   if (b->status != LBC_OK) return b->status;
   B->members.push_back({b, steps, false});

@@ -36,6 +36,22 @@ struct LBArgs {
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,
                     cudaStream_t s);
 
+// Thermal fluctuations of the LB step (Eq. [mrt-fluct]): the non-equilibrium
+// part of moment k (4..18) relaxes by gk[group of k] and is kicked by
+// psi_k sqrt(rho) r_k, psi_k = phi_k / b_k in the normalised moments
+// (sum_i e_ki v_i) / b_k, r_k standard normal from Philox4x32-10 with counter
+// (cell, step, 0, k / 4) and key (key0, key1); step is read from *step.
+struct FluctArgs {
+  Real gk[5];                         // per relaxation group (group 0 unused)
+  Real psi[Q];
+  uint32_t key0, key1;
+  const unsigned long long* step;
+};
+// the fluctuating LB step (FP32 / FP64 storage), then the step counter
+// advanced by one
+void launch_lb_fluct(int storage, const void* fin, void* fout, const LBArgs& a,
+                     const FluctArgs& t, unsigned long long* step, cudaStream_t s);
+
 // One entry of a batched LB launch: a box's arguments, its source and
 // destination population arrays, and its first row in the launch (rows =
 // ny nz per box, in table order; x-rows of at most 128 cells).

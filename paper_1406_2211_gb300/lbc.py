@@ -96,6 +96,7 @@ _PROTOS = {
     "lbc_box_status": (_S, [_P]),
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
     "lbc_box_get_option": (_S, [_P, C.c_int32, C.POINTER(C.c_int64)]),
+    "lbc_box_set_thermal": (_S, [_P, C.c_double, C.c_uint64]),
     "lbc_box_launches_per_step": (C.c_int64, [_P]),
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
     "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
@@ -313,6 +314,11 @@ class Box:
 
     def set_option(self, option, value):
         check(self.lib.lbc_box_set_option(self.handle, option, value), "lbc_box_set_option")
+
+    def set_thermal(self, kT, seed=0):
+        """Thermal fluctuations of the fluid at temperature kT (0: off)."""
+        check(self.lib.lbc_box_set_thermal(self.handle, float(kT), int(seed)),
+              "lbc_box_set_thermal")
 
     def get_option(self, option):
         v = C.c_int64()

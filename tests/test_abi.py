@@ -150,3 +150,4 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbc_box_autotune(None, None, None, None) == lbc.LBC_ERR_ARG
     assert lib.lbc_box_set_option(None, lbc.LBC_OPT_NODE_MOMENTS, 1) == lbc.LBC_ERR_ARG
     assert lib.lbc_box_get_option(None, lbc.LBC_OPT_NODE_MOMENTS, C.byref(n)) == lbc.LBC_ERR_ARG
+    assert lib.lbc_box_set_thermal(None, 1e-4, 1) == lbc.LBC_ERR_ARG
