@@ -211,8 +211,6 @@ lbc_status lbc_box_step(lbc_box* box, int64_t nsteps, void* stream);
 lbc_status lbc_box_get_fields(lbc_box* box, double* rho_host, double* u_host,
                               void* stream);
 
-/* Particle positions, velocities and last hydrodynamic force F^h (host
- * [n][3] each, any may be NULL).  For IBM, force_h is the spread force. */
 /* Viscous stress of the current state, Eq. [viscstress] (first line):
  * sigma = 1/2 (1 + (1 - Lambda_1/2)^2) sum_i (fbar_i - f_i^eq) c_i c_i of
  * the post-streaming populations, in FP64, as host array sigma[6][nz][ny][nx]
@@ -221,6 +219,8 @@ lbc_status lbc_box_get_fields(lbc_box* box, double* rho_host, double* u_host,
  * population array as staging. */
 lbc_status lbc_box_get_stress(lbc_box* box, double* sigma, void* stream);
 
+/* Particle positions, velocities and last hydrodynamic force F^h (host
+ * [n][3] each, any may be NULL).  For IBM, force_h is the spread force. */
 lbc_status lbc_box_get_particles(lbc_box* box, double* pos, double* vel,
                                  double* force_h, void* stream);
 

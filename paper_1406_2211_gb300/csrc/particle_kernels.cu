@@ -15,12 +15,12 @@
 // population storage (double for FP64 storage, float otherwise), because
 // FP64 arithmetic is a small fraction of the FP32 rate on this GPU.
 //
-// Spreading is a gather over force tiles of 8^3 cells: one warp owns one
-// tile, scans the markers binned into the neighbouring tiles 32 at a time
-// with a cheap reach test on their stencil base (ballot), and accumulates the
-// survivors one after another into shared memory; every node of a tile is
-// written by one lane per marker, so no atomics are used and the summation
-// order is fixed (markers sorted by tile, tiles in a fixed order).
+// Spreading is a gather over force tiles of 4^3 cells: one warp owns one
+// live tile, tests the markers binned into the neighbouring tiles with a
+// cheap reach test on their stencil base (ballot), and adds the survivors one
+// after another into per-lane register sums (each lane owns two cells of the
+// tile), so no atomics are used and the summation order is fixed (markers
+// sorted by tile, tiles in a fixed order).
 //
 // Markers are binned once per step; the bins stay valid while a marker is
 // within one cell of its home tile (a marker moves |v| h << 1 per step in

@@ -133,8 +133,9 @@ def test_spreading_is_deterministic():
 
 def test_point_particle_32_fp64():
     """32^3 FP64 BGK tau = 0.8, one particle with force coupling gamma = m = 1,
-    trilinear, v0 = (0.01, 0, 0): second- and first-order schemes against the
-    oracle, and conservation of m v0 in the periodic box."""
+    trilinear, v0 = (0.01, 0, 0), the workload's full 1000 steps: second- and
+    first-order schemes against the oracle, and conservation of m v0 in the
+    periodic box."""
     require_cuda()
     c = synth.config("fc_point_particle_32")
     nx, ny, nz = c["box"]
@@ -142,7 +143,7 @@ def test_point_particle_32_fp64():
     from oracle import lattice as OLat
     fbar0 = OLat.equilibrium(np.ones(shape), np.zeros((3,) + shape))
     parts = dict(pos=np.array([c["particle"]]), vel=np.array([c["velocity"]]), mass=1.0)
-    for order, steps in ((2, 300), (1, 100)):
+    for order, steps in ((2, c["steps"]), (1, c["steps"])):
         box, sm = make_pair(shape, fbar0, coll="bgk", tau=c["tau"], storage="f64",
                             kind="fc", order=order, stencil="trilinear",
                             gamma=c["gamma"], parts=parts)
@@ -161,8 +162,9 @@ def test_point_particle_32_fp64():
 def test_reduced_mrt_bead_chains():
     """The 256^3 chain workload at 1/4 size: 64^3 MRT FP32, bead chains with
     k = 10 bonds, force coupling gamma = 5, body force 1e-6, the multiple
-    time-step split of Sec. 6 (Eq. [multistep]) with n = 2.  FP32 storage and
-    FP32 interpolation/spreading: 1e-6 on positions, 1e-5 relative L2 on
+    time-step split of Sec. 6 (Eq. [multistep]) with n = 4 coupled sub-steps
+    per half step, as in the full workload.  FP32 storage and FP32
+    interpolation/spreading: 1e-6 on positions, 1e-5 relative L2 on
     velocities."""
     require_cuda()
     c = synth.config("mrt_bead_chains_256", scale=4)
@@ -187,6 +189,44 @@ def test_reduced_mrt_bead_chains():
     assert rel_l2(vel_g, sm.parts.vel) < 1e-5
     _, u = box.get_fields()
     assert rel_l2(u, sm.fluid_velocity()) < 1e-5
+    box.close()
+
+
+@pytest.mark.slow
+def test_bead_chains_32_tau08_1000_steps():
+    """The 256^3 chain workload at 1/8 size (32^3, 4 chains of 50 beads: the
+    same bead density), with a collision that relaxes: MRT at tau = 0.8 (shear
+    eigenvalue 1 - 1/tau = -0.25; ghosts fully relaxed, as in the workload),
+    FP32 deviations, Eq. [multistep] with n = 4, over 1000 steps.  The FP32
+    accuracy bar on a coupled box: relative L2 error of the fluid velocity at
+    most 1e-5 after 1000 steps; particle positions element by element within
+    2e-6 (FP32 node velocities, a few 1e-7 relative, integrated over 1000
+    steps of a drift of order 0.5 lattice units)."""
+    require_cuda()
+    c = synth.config("mrt_bead_chains_256", scale=8)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    pos, bonds = synth.bead_chains(c["nchains"], c["beads"], c["box"], c["bond_r0"],
+                                   seed=c["seed"])
+    parts = dict(pos=pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
+                 bond_k=c["bond_k"], bond_r0=c["bond_r0"])
+    from oracle import lattice as OLat
+    fbar0 = OLat.equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=c["body_force"],
+                        storage="f32", kind="fc", stencil="trilinear", gamma=c["gamma"],
+                        split=c["mode"], n=c["substeps"], parts=parts)
+    steps = 1000
+    box.step(steps)
+    for _ in range(steps):
+        sm.step()
+    pos_g, vel_g, _ = box.get_particles()
+    d = OC.min_image(pos_g - sm.parts.pos, shape, False)
+    assert np.abs(d).max() < 2e-6, np.abs(d).max()
+    assert rel_l2(vel_g, sm.parts.vel) < 1e-5
+    _, u = box.get_fields()
+    assert rel_l2(u, sm.fluid_velocity()) < 1e-5
+    m, P, st = box.invariants()
+    assert st == 0
     box.close()
 
 

@@ -1,6 +1,7 @@
 """Pins of the fluctuating collision (Sec. 3.2, Eq. [mrt-fluct]) in the oracle.
 
-* The counter-based generator: uniform outputs (chi-square), every output
+* The counter-based generator: the published Philox4x32-10 known-answer
+  vectors (tests/golden/philox4x32_10_kat.txt), uniform outputs (chi-square), every output
   bit balanced, one flipped counter bit changes about half the output bits
   (ten rounds of mixing), distinct counters give distinct outputs, and the
   Box-Muller Gaussians have the normal's first four moments.
@@ -21,6 +22,25 @@ import synth
 from oracle import fluct as F
 from oracle import lattice as L
 from oracle import lb as OL
+
+
+def test_philox_known_answer_vectors():
+    """The three published Philox4x32-10 known-answer vectors (counter, key ->
+    output) of the Random123 distribution: a wrong round constant, key
+    increment, word permutation or round count changes every output."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(t, 16) for t in row]
+        ctr = [np.array([c], dtype=np.uint64) for c in v[:4]]
+        out = F.philox4x32(ctr, (v[4], v[5]))
+        assert [int(w[0]) for w in out] == v[6:10]
+    # nine rounds is not Philox4x32-10
+    v = [int(t, 16) for t in rows[2]]
+    out9 = F.philox4x32([np.array([c], dtype=np.uint64) for c in v[:4]], (v[4], v[5]), rounds=9)
+    assert [int(w[0]) for w in out9] != v[6:10]
 
 
 def test_uniforms_are_uniform():

@@ -193,3 +193,118 @@ def test_couette_linear():
         sm.step()
     u = sm.fluid_velocity()[0, :, 0, 0]
     assert np.abs(u - exact).max() < 1e-10 * abs(ut)
+
+
+# ---------------------------------------------------------------- MRT groups
+# The pins above see only the shear rate (shear wave, Couette stress, the
+# Poiseuille second difference) or compare MRT with itself (equal rates ==
+# BGK).  The two tests below pin which moments the oracle relaxes with the
+# bulk rate and with each ghost rate, against facts that do not depend on
+# the oracle's basis or group table:
+#   * sound attenuation.  Linearised Navier-Stokes with shear viscosity nu
+#     and bulk viscosity nu_b damps a longitudinal wave of wavenumber k at
+#     the rate Gamma = k^2 (2 nu / 3 + nu_b / 2).  For a lattice-Boltzmann
+#     fluid whose stress trace relaxes at lambda_b and whose traceless stress
+#     relaxes at lambda_s, nu = cs2 (1/lambda_s - 1/2) and
+#     nu_b = (2/3) cs2 (1/lambda_b - 1/2) (Duenweg, Schiller and Ladd, Phys.
+#     Rev. E 76, 036704 (2007), eta_b = rho cs2 h (1 + gamma_b)/(3 (1 -
+#     gamma_b))).  Moment 4 relaxed at the shear rate would give nu_b of
+#     lambda_s instead.
+#   * the k = 0 spectrum.  On one periodic cell the step is the collision
+#     alone; the 19 populations split into the 4 conserved moments, the
+#     stress (1 trace + 5 traceless), and 9 kinetic ("ghost") modes, 6 odd
+#     and 3 even under c -> -c.  With four distinct rates the eigenvalues
+#     1 - lambda come with multiplicities 1 (bulk), 5 (shear), 6 (odd
+#     ghosts), 3 (even ghosts), and each eigenspace has the stated parity.
+#     Swapped ghost groups would give multiplicities 3 and 6.
+
+
+def _linear_step_matrix(p, L_):
+    """19 x 19 complex matrix of one recombined step acting on a plane-wave
+    perturbation exp(i k x), k = 2 pi / L_, of a fluid at rest (rho = 1),
+    built column by column from one real run each: the response to
+    delta_ij cos(k x) projected on cos gives Re M[:, j], on sin gives
+    -Im M[:, j]."""
+    shape = (1, 1, L_)
+    x = np.arange(L_)
+    k = 2 * np.pi / L_
+    base = L.equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    zero = np.zeros((3,) + shape)
+    eps = 1e-7
+    M = np.zeros((19, 19), dtype=np.complex128)
+    cosk, sink = np.cos(k * x), np.sin(k * x)
+    for j in range(19):
+        f = base.copy()
+        f[j, 0, 0, :] += eps * cosk
+        r = (lb.step_recombined(f, zero, zero, p) - base)[:, 0, 0, :] / eps
+        M[:, j] = (r @ cosk) * (2.0 / L_) - 1j * (r @ sink) * (2.0 / L_)
+    return M
+
+
+def _sound_damping(p, L_):
+    """Gamma / k^2 of the least damped complex-conjugate pair (sound)."""
+    mu = np.linalg.eigvals(_linear_step_matrix(p, L_))
+    cplx = mu[np.abs(mu.imag) > 1e-6]
+    best = cplx[np.argmax(np.abs(cplx))]
+    k2 = (2 * np.pi / L_) ** 2
+    return -np.log(np.abs(best)) / k2
+
+
+@pytest.mark.parametrize("lam_s,lam_b", [(1.25, 0.6), (0.8, 1.5), (1.0, 1.0)])
+def test_sound_attenuation_pins_bulk_rate(lam_s, lam_b):
+    p = lb.LBParams(collision="mrt", tau=1.0, mrt_lambda=(lam_s, lam_b, 1.3, 0.7))
+    L1, L2 = 64, 128
+    g1, g2 = _sound_damping(p, L1), _sound_damping(p, L2)
+    k1, k2 = (2 * np.pi / L1) ** 2, (2 * np.pi / L2) ** 2
+    g0 = (g1 * k2 - g2 * k1) / (k2 - k1)          # Richardson in k^2
+    nu = (1.0 / lam_s - 0.5) / 3.0
+    nu_b = (2.0 / 3.0) * (1.0 / lam_b - 0.5) / 3.0
+    expect = 2.0 * nu / 3.0 + nu_b / 2.0
+    assert abs(g0 / expect - 1.0) < 1e-4
+    if lam_b != lam_s:
+        # what the same wave would give with the trace relaxed at the shear rate
+        wrong = 2.0 * nu / 3.0 + (2.0 / 3.0) * (1.0 / lam_s - 0.5) / 3.0 / 2.0
+        assert abs(g0 / wrong - 1.0) > 1e-2
+
+
+def test_zero_wavenumber_spectrum_pins_ghost_groups():
+    lam = {"shear": 1.3, "bulk": 0.6, "odd": 1.7, "even": 0.45}
+    p = lb.LBParams(collision="mrt", tau=1.0,
+                    mrt_lambda=(lam["shear"], lam["bulk"], lam["odd"], lam["even"]))
+    # one cell: streaming is the identity, the step is the collision
+    shape = (1, 1, 1)
+    base = L.equilibrium(np.ones(shape), np.zeros((3,) + shape))
+    zero = np.zeros((3,) + shape)
+    eps = 1e-7
+    M = np.zeros((19, 19))
+    for j in range(19):
+        f = base.copy()
+        f[j] += eps
+        M[:, j] = (lb.step_recombined(f, zero, zero, p) - base)[:, 0, 0, 0] / eps
+    mu, vecs = np.linalg.eig(M)
+    assert np.abs(mu.imag).max() < 1e-9
+    mu = mu.real
+    expect = {"conserved": (1.0, 4), "bulk": (1 - lam["bulk"], 1),
+              "shear": (1 - lam["shear"], 5), "odd": (1 - lam["odd"], 6),
+              "even": (1 - lam["even"], 3)}
+    for name, (val, mult) in expect.items():
+        sel = np.abs(mu - val) < 1e-6
+        assert sel.sum() == mult, (name, val, np.sort(mu))
+        V = vecs[:, sel].real
+        flipped = V[L.OPP]
+        if name == "odd":
+            assert np.abs(flipped + V).max() < 1e-6 * np.abs(V).max()
+        elif name in ("even", "bulk", "shear"):
+            assert np.abs(flipped - V).max() < 1e-6 * np.abs(V).max()
+        if name == "even":
+            # kinetic modes carry no density, momentum or stress: orthogonal
+            # to every polynomial of degree <= 2 in c
+            polys = [np.ones(19)] + [L.CF[:, a] for a in range(3)] + \
+                    [L.CF[:, a] * L.CF[:, b] for a in range(3) for b in range(a, 3)]
+            for q in polys:
+                assert np.abs(q @ V).max() < 1e-6 * np.abs(V).max()
+        if name == "shear":
+            # traceless stress: no trace, no density
+            c2 = (L.CF ** 2).sum(axis=1)
+            assert np.abs(c2 @ V).max() < 1e-6 * np.abs(V).max()
+            assert np.abs(np.ones(19) @ V).max() < 1e-6 * np.abs(V).max()
