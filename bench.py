@@ -175,7 +175,7 @@ def run_gpu(args, rank, world, local_rank):
     M, B = len(pos), len(bonds)
     stream = torch.cuda.current_stream()
 
-    def timed(storage, steps, sample_clocks, tau=None):
+    def timed(storage, steps, sample_clocks, tau=None, prep=None):
         """Warm up, then time `steps` coupled steps of a fresh box (CUDA
         events on the launching stream, barrier + synchronize on both sides);
         LB kernel launches are timed by event nodes inside the graphs."""
@@ -185,6 +185,7 @@ def run_gpu(args, rank, world, local_rank):
         box.set_particles(pos, vel=np.zeros_like(pos), mass=c["mass"], bonds=bonds,
                           bond_k=c["bond_k"], bond_r0=c["bond_r0"])
         shape = box.autotune()           # LB launch shape, before any timing
+        keep = prep(box) if prep else None   # a variant's set-up (kept alive)
         box.step(args.warmup)
         box.set_option(lbc.LBC_OPT_TIMING, steps + 4)
         # the graphs are recaptured with timing nodes: one eager step + one
@@ -211,6 +212,7 @@ def run_gpu(args, rank, world, local_rank):
         r["ms"] = e0.elapsed_time(e1)
         r["clocks"] = clocks.stop() if clocks else None
         r["lb_ms"], r["lb_n"] = box.lb_timing(reset=True)
+        del keep
         _, _, st = box.invariants()
         if st != 0:
             raise RuntimeError("non-finite state after the timed steps (%s)" % storage)
@@ -249,15 +251,26 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_forms:
         forms = {}
         nform = min(args.steps, 100)
-        for name, st16, tau in (("f16dev", "f16dev", None), ("bf16dev", "bf16dev", None),
-                                ("f32_tau0.8", "f32", 0.8)):
-            r = timed(st16, nform, False, tau=tau)
+        # thermal fluctuations (Eq. [mrt-fluct] kicks inside the fused LB
+        # kernel, random force zeta on the beads) at k_B T = 1e-7, and the
+        # FP32 step with the stress epilogue (Eq. [viscstress]: 6 FP32
+        # values more per cell, 176 B per cell update)
+        thermal = lambda box: box.set_thermal(1e-7, 2014)
+        stress = lambda box: box.stress_output()
+        for name, st16, tau, prep, extra in (
+                ("f16dev", "f16dev", None, None, 0), ("bf16dev", "bf16dev", None, None, 0),
+                ("f32_tau0.8", "f32", 0.8, None, 0), ("f32_thermal", "f32", None, thermal, 0),
+                ("bf16dev_thermal", "bf16dev", None, thermal, 0),
+                ("f32_stress", "f32", None, stress, 24)):
+            r = timed(st16, nform, False, tau=tau, prep=prep)
+            alg = BYTES_PER_CELL[st16] + extra
+            lb_gbs = alg * cells / (r["lb_avg_ms"] * 1e-3) / 1e9
             forms[name] = {"value": r["value"], "unit": "MLUPS", "steps": nform,
                            "ms_per_step": r["ms_max"] / nform, "tau": tau or c["tau"],
-                           "lb_avg_ms": r["lb_avg_ms"], "lb_achieved_gbs": r["achieved"],
-                           "lb_frac_of_peak": r["achieved"] / peak,
+                           "lb_avg_ms": r["lb_avg_ms"], "lb_achieved_gbs": lb_gbs,
+                           "lb_frac_of_peak": lb_gbs / peak,
                            "step_frac": r["step_gbs"] / peak,
-                           "alg_bytes_per_cell": BYTES_PER_CELL[st16], "lb_block": r["lb_block"]}
+                           "alg_bytes_per_cell": alg, "lb_block": r["lb_block"]}
 
     # end to end through the C ABI with host buffers: upload particles,
     # step, read particles and invariants back (copies inside the timing)

@@ -24,8 +24,9 @@
  *    stream).  Calls enqueue work on it and return; getters (lbc_box_get_*,
  *    lbc_box_invariants) synchronise that stream before returning.
  *  - Errors are returned as lbc_status codes; no C++ exception crosses this
- *    interface.  A device-detected error (non-finite density found by
- *    lbc_box_invariants) is latched in the box and returned by
+ *    interface.  A device-detected error (a non-finite density met by an LB
+ *    step, a marker that left its bin) is latched in the box by
+ *    lbc_box_check() or lbc_box_invariants() and returned by
  *    lbc_box_status() and by every later lbc_box_step().
  *  - Layouts: cell (x, y, z) sits at position (x, y, z); fields are dense
  *    with x fastest: rho[(z*ny + y)*nx + x], u[c][(z*ny + y)*nx + x] with
@@ -230,8 +231,21 @@ lbc_status lbc_box_get_particles(lbc_box* box, double* pos, double* vel,
 lbc_status lbc_box_invariants(lbc_box* box, double* mass, double* momentum,
                               void* stream);
 
-/* Latched device status of the box (LBC_OK or the first error seen). */
+/* Latched status of the box (LBC_OK or the first error seen); does not
+ * touch the device. */
 lbc_status lbc_box_status(const lbc_box* box);
+
+/* Failure detection in the step path: every LB step sets a device health
+ * flag when it meets a non-finite density (NaN or infinity anywhere in a
+ * cell's populations reaches its density), and the interpolations set the
+ * particle status word when a marker leaves its bin.  This call synchronises
+ * `stream`, reads both words and latches LBC_ERR_NONFINITE or LBC_ERR_STATE
+ * into the box's status, which it returns; later lbc_box_step calls then
+ * return it too.  Replacing the state (lbc_box_init_equilibrium,
+ * lbc_box_set_fields, lbc_box_set_populations) clears the flag and a latched
+ * LBC_ERR_NONFINITE.  Batches read their members' flags without waiting
+ * (lbc_batch_advance). */
+lbc_status lbc_box_check(lbc_box* box, void* stream);
 
 /* Options:
  *  LBC_OPT_GRAPHS  1 = replay steps as captured CUDA graphs (default), 0 =
@@ -261,31 +275,68 @@ lbc_status lbc_box_status(const lbc_box* box);
  *                  two differ only in the order of the floating-point sum.
  * Errors: LBC_ERR_ARG for an unknown option or value, LBC_ERR_STATE for a
  * batch member.  Setting an option drops the captured step graphs. */
+/*  LBC_OPT_THERMAL_AMPLITUDE  0 = the stationary kick amplitude of
+ *                  lbc_box_set_thermal (default), 1 = the amplitude as
+ *                  printed in Eq. [mrt-fluct], sqrt(mu b_k lambda_k^2) (it
+ *                  does not keep the moments at their equilibrium variance
+ *                  unless lambda_k = 1; for comparison runs). */
 #define LBC_OPT_GRAPHS 1
 #define LBC_OPT_TIMING 2
 #define LBC_OPT_NODE_MOMENTS 3
 #define LBC_OPT_GATHER_LANES 4
+#define LBC_OPT_THERMAL_AMPLITUDE 5
 lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
 
 /* Current value of an option (LBC_OPT_TIMING: the event pairs reserved). */
 lbc_status lbc_box_get_option(const lbc_box* box, int32_t option, int64_t* value);
 
-/* Thermal fluctuations of the fluid (Sec. 3.2, Eq. [mrt-fluct]): from the
- * next step on, every LB step kicks the non-equilibrium part of each
- * non-conserved moment k (in the MRT basis; BGK uses the same form with one
- * eigenvalue) by sqrt(rho) phi_k r_k, phi_k^2 = mu b_k (1 - gamma_k^2),
- * mu = k_B T / (a^3 cs2), gamma_k = 1 - lambda_k, r_k standard normal.  (The
- * paper prints phi_k = sqrt(mu b_k lambda_k^2); the form used keeps the
- * moments at their equilibrium variance mu rho b_k.)  The r_k come from
- * Philox4x32-10 with counter (x + nx (y + ny z), step, 0, k / 4) and key
- * (low, high 32 bits of seed), Box-Muller pairs (cos, sin) of uniforms
- * (0, 1) and (2, 3) of a block giving r_{4 block} .. r_{4 block + 3}; the
- * step counter restarts at 0 here and advances once per LB step.
- * kT = 0 switches the fluctuations off.  Particle (coupling) noise is not
- * included.  Errors: LBC_ERR_ARG for kT < 0 or non-finite; LBC_ERR_STATE for
- * a batch member or 16-bit storage with kT > 0 (thermal boxes cannot join a
- * batch).  Drops the captured step graphs. */
+/* Thermal fluctuations (Sec. 3.2, Eq. [mrt-fluct]; Sec. 5.2,
+ * Eq. [viscous-coupling]): from the next step on, every LB step kicks the
+ * non-equilibrium part of each non-conserved moment k (in the MRT basis; BGK
+ * uses the same form with one eigenvalue) by sqrt(rho) phi_k r_k,
+ * phi_k^2 = mu b_k (1 - gamma_k^2), mu = k_B T / (a^3 cs2),
+ * gamma_k = 1 - lambda_k, r_k standard normal (the paper prints
+ * phi_k = sqrt(mu b_k lambda_k^2); the form used keeps the moments at their
+ * equilibrium variance mu rho b_k; LBC_OPT_THERMAL_AMPLITUDE selects the
+ * printed one).  Force-coupled particles (LBC_FC, LBC_EBF) get the random
+ * force zeta of Eq. [modified-force] in every coupling (sub-)step of length
+ * s: three independent normals of variance 2 k_B T gamma / s (EBF:
+ * gamma = rho0 a^3 / h), added as F^h = -[gamma (v - u) - zeta + alpha/2
+ * F_int] / D (first order: F^h = -gamma (v - u) + zeta); the fluid receives
+ * -F^h, so momentum stays conserved.  The modified EBF has no random force
+ * (its no-slip condition fixes F^h).
+ * Random numbers: Philox4x32-10, key = (low, high 32 bits of seed); fluid:
+ * counter (x + nx (y + ny z), step, 0, k / 4), Box-Muller pairs (cos, sin)
+ * of uniforms (0, 1) and (2, 3) of a block giving r_{4 block} ..
+ * r_{4 block + 3}; particles: counter (particle index, step, 8 + sub-step,
+ * 0), the first three normals of the block, sub-steps numbered 0, 1 for the
+ * two half steps (0 .. 2n - 1 for the multiple-time-step split with the
+ * coupling inside, 0 for first order).  `step` counts thermal LB steps in
+ * device memory: it starts at 0 when a seed is first given or changes, and
+ * keeps running when the fluctuations are switched off and on again with the
+ * same seed (steps without fluctuations do not advance it), so no kick is
+ * repeated.  kT = 0 switches the fluctuations off.
+ * Errors: LBC_ERR_ARG for kT < 0 or non-finite; LBC_ERR_STATE for a batch
+ * member (switch before joining; thermal boxes may join batches);
+ * LBC_ERR_UNSUPPORTED with a stress output set, or for 2^31 or more stored
+ * population values.  Drops the captured step graphs; needs no device
+ * synchronisation (the counter is reset on the stream of the next step). */
 lbc_status lbc_box_set_thermal(lbc_box* box, double kT, uint64_t seed);
+
+/* Stress output (Eq. [viscstress], first line): with sigma_dev set, every LB
+ * step also writes the viscous stress of the populations it collides (the
+ * post-streaming state at the start of that step),
+ * sigma = 1/2 (1 + (1 - Lambda_1/2)^2) sum_i (fbar_i - f_i^eq) c_i c_i, the
+ * trace relaxed with the bulk and the traceless part with the shear
+ * eigenvalue, into the caller's device array sigma_dev[6][nz][ny][nx]
+ * (components xx, yy, zz, xy, yz, xz; FP64 for FP64 storage, FP32
+ * otherwise; momentum-flux sign as lbc_box_get_stress), in the same kernel
+ * (no extra pass over the populations).  NULL stops it.  The caller owns the
+ * array (16-byte aligned, at least 6 nx ny nz elements: LBC_ERR_OOM) and
+ * reads it after the step on its stream.  Errors: LBC_ERR_STATE for a batch
+ * member; LBC_ERR_UNSUPPORTED with thermal fluctuations on, or for 2^31 or
+ * more stored population values.  Drops the captured step graphs. */
+lbc_status lbc_box_set_stress_output(lbc_box* box, void* sigma_dev, size_t bytes);
 
 /* Sum of the event-measured durations (ms) of the LB kernel launches timed
  * since the last reset, and their count; waits for the last event.
@@ -327,8 +378,11 @@ size_t lbc_box_population_bytes(const lbc_box* box);
  * run with the same per-box arguments, so a box advanced in a batch matches
  * the same box advanced in a batch of its own bit for bit.
  *
+ * Thermal boxes (lbc_box_set_thermal) may be members; their LB steps form
+ * groups of their own.
+ *
  * Limits: x-rows of at most LBC_BATCH_MAX_NX cells; boxes must have been
- * created without LBC_OPT_TIMING.  The batch owns no device memory: the
+ * created without LBC_OPT_TIMING and without a stress output.  The batch owns no device memory: the
  * caller passes an arena of lbc_batch_bytes_required(max_boxes) bytes. */
 typedef struct lbc_batch lbc_batch;
 #define LBC_BATCH_MAX_NX 128
@@ -346,8 +400,8 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
 
 /* Admit a box with a budget of `steps` time steps (>= 1).  Errors:
  * LBC_ERR_OOM (no free slot), LBC_ERR_ARG (NULL, steps < 1, nx >
- * LBC_BATCH_MAX_NX), LBC_ERR_STATE (the box is in a batch already or has
- * LBC_OPT_TIMING set). */
+ * LBC_BATCH_MAX_NX), LBC_ERR_STATE (the box is in a batch already, has
+ * LBC_OPT_TIMING set or a stress output). */
 lbc_status lbc_batch_add(lbc_batch* batch, lbc_box* box, int64_t steps);
 
 /* Remove a member before its budget is spent (its state is that of the
@@ -361,7 +415,13 @@ lbc_status lbc_batch_remaining(const lbc_batch* batch, const lbc_box* box, int64
  * steps, enqueued on `stream` (asynchronous).  Members whose budget reaches
  * zero leave the batch and are written to finished[0 .. *nfinished) (room
  * for max_boxes entries); their results can then be read with the box
- * getters.  *steps_done receives k (0 for an empty batch). */
+ * getters.  Failed members leave too, without stopping the others: at the
+ * start of each call the health flags the previous call copied to pinned
+ * host memory are read if those copies are done (no waiting), a member
+ * whose LB steps met a non-finite density gets LBC_ERR_NONFINITE, and every
+ * member whose status is not LBC_OK is written to finished[] before the
+ * others advance (check lbc_box_status of each finished box).  *steps_done
+ * receives k (0 for an empty batch). */
 lbc_status lbc_batch_advance(lbc_batch* batch, int64_t max_steps, void* stream,
                              lbc_box** finished, int32_t* nfinished, int64_t* steps_done);
 
@@ -376,19 +436,23 @@ lbc_status lbc_batch_destroy(lbc_batch* batch);
  * memory, for callers that cannot allocate: it calls no cudaMalloc and needs
  * no arena, because its scratch is a fixed file-scope device array of
  * LBC_NOALLOC_MAX_PLANES x 4 doubles (128 KB, held on every device that
- * loads the library until the process exits).  Typical callers are code
- * running while a CUDA graph is captured, processes whose device memory is
- * fully reserved by a pool, and monitoring hooks holding someone else's
- * buffer.  The paper has no counterpart: this is a library service.
+ * loads the library until the process exits).  Typical callers are
+ * processes whose device memory is fully reserved by a pool or by another
+ * framework, and monitoring hooks that only hold a pointer to someone
+ * else's buffer and have no allocator to ask.  The paper has no
+ * counterpart: this is a library service.
  *   fbar_dev  device FP64 array [19][nz][ny][nx] of full populations (the
  *             layout lbc_box_get_populations() writes to the host)
  *   out_dev   device FP64 array of 4: sum of all populations (mass) and the
  *             momentum sum_i f_i c_i (x, y, z)
  * Returns LBC_ERR_ARG for NULL pointers, non-positive sizes or
  * nz > LBC_NOALLOC_MAX_PLANES.  The first call on a device looks up the
- * scratch address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the scratch: calls whose kernels overlap
- * on the GPU (different streams or threads) race and must be serialised. */
+ * scratch address (cudaGetSymbolAddress) and keeps it for that device;
+ * make that first call before any stream capture.  The kept address belongs
+ * to the device's current context: do not use this entry point across a
+ * device reset (cudaDeviceReset) in the same process.  All calls share the
+ * scratch: calls whose kernels overlap on the GPU (different streams or
+ * threads) race and must be serialised. */
 #define LBC_NOALLOC_MAX_PLANES 4096
 lbc_status lbc_fbar_moments_noalloc(const double* fbar_dev, int32_t nx, int32_t ny,
                                     int32_t nz, double* out_dev, void* stream);

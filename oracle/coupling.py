@@ -196,12 +196,16 @@ def intrinsic_forces(parts, pos, shape, walls):
 
 
 def coupling_force(kind, order, v, u, Fint, mass, s, gamma, rho0,
-                   include_int=True):
+                   include_int=True, zeta=None):
     """Hydrodynamic force F^h on each particle for a (sub-)step of length s.
 
     kind in ('fc', 'ebf', 'mebf'); v, u, Fint (M, 3); mass (M,).
     include_int=False gives the coupling-only operator F_h of the split in
-    Sec. 6 (intrinsic forces integrated separately).
+    Sec. 6 (intrinsic forces integrated separately).  zeta (M, 3): the
+    random force of Eq. [viscous-coupling], entering the midpoint force of
+    Eq. [modified-force] as -[gamma (v - u) - zeta + alpha/2 F_int] / D, and
+    the explicit first-order force as -gamma (v - u) + zeta.  The modified
+    EBF takes none (its no-slip condition determines F^h).
     """
     m = mass[:, None]
     Fi = Fint if include_int else np.zeros_like(Fint)
@@ -211,8 +215,11 @@ def coupling_force(kind, order, v, u, Fint, mass, s, gamma, rho0,
         r = 1.0 / (1.0 + m / rho0)
         return -(v - u) / (s * (1.0 / m + 1.0 / rho0)) - r * Fi
     if order == 1:
-        return -gamma * (v - u)
+        F = -gamma * (v - u)
+        return F if zeta is None else F + zeta
     alpha = gamma * s / m
     beta = gamma * s / rho0
     D = 1.0 + 0.5 * alpha + 0.5 * beta
-    return -(gamma * (v - u) + 0.5 * alpha * Fi) / D
+    if zeta is None:
+        return -(gamma * (v - u) + 0.5 * alpha * Fi) / D
+    return -((gamma * (v - u) + 0.5 * alpha * Fi) - zeta) / D

@@ -95,6 +95,18 @@ def gaussians(cells, step, stream, count, seed):
     return out.reshape(4 * nblk, n)[:count]
 
 
+def particle_noise(nparticles, step, substep, s, gamma, kT, seed):
+    """Random force zeta of the force coupling for one coupling (sub-)step of
+    length s (Sec. 5.2, Eq. [viscous-coupling]): white noise of intensity
+    <zeta_a(t) zeta_b(t')> = 2 k_B T gamma delta_ab delta(t - t') averaged
+    over the step, i.e. independent normals of variance 2 k_B T gamma / s
+    per component (the fluctuation-dissipation relation of the friction
+    gamma).  Counter (particle index, step, 8 + substep, 0); the components
+    are the first three Gaussians of the block.  Returns (M, 3)."""
+    r = gaussians(np.arange(nparticles), step, 8 + substep, 3, seed)   # (3, M)
+    return np.sqrt(2.0 * kT * gamma / s) * r.T
+
+
 def amplitudes(gam, kT, printed=False):
     """phi_k for the eigenvalues gam_k = 1 - lambda_k (0 for the conserved
     moments).  printed=True takes the amplitude as printed in the paper,

@@ -43,6 +43,7 @@ from . import lattice as L
 from . import lb
 from . import delta
 from . import coupling as CP
+from . import fluct
 
 
 class CouplingParams:
@@ -75,9 +76,38 @@ class Sim:
         self.lb_form = lb_form
         self.last_Fh = None
         self.t = 0
+        self.kT = 0.0            # thermal fluctuations (set_thermal)
+        self.seed = None
+        self.tstep = 0           # thermal LB steps since the seed was set
+        self.printed = False
+
+    def set_thermal(self, kT, seed=0, printed=False):
+        """Thermal fluctuations at k_B T (0: off): the fluctuating collision
+        of Eq. [mrt-fluct] (stationary amplitude, or the printed one) and the
+        random force zeta of force-coupled particles (FC and original EBF).
+        The thermal step counter restarts when the seed changes and keeps
+        running otherwise (steps without fluctuations do not advance it)."""
+        if kT > 0.0 and seed != self.seed:
+            self.tstep = 0
+            self.seed = seed
+        self.kT = float(kT)
+        self.printed = bool(printed)
 
     # ----------------------------------------------------------- helpers
     def _lb(self, Fa, Fb):
+        if self.kT > 0.0:
+            zero = np.zeros((3,) + self.shape)
+            if self.cpl.order == 1:
+                # first order: the whole force F_b for the step (u1 = u0 + (F + g)/rho)
+                Fa = Fb = zero if Fb is None else Fb
+            if self.lb_form == 'literal':
+                out = fluct.step_literal_fluct(self.fbar, Fa, Fb, self.p, self.kT, self.seed,
+                                               self.tstep)
+            else:
+                out = fluct.step_recombined_fluct(self.fbar, Fa, Fb, self.p, self.kT, self.seed,
+                                                  self.tstep, self.printed)
+            self.tstep += 1
+            return out
         if self.cpl.order == 1:
             return lb.step_first_order(self.fbar, Fb, self.p)
         if self.lb_form == 'literal':
@@ -110,14 +140,21 @@ class Sim:
     def _fint(self, pos):
         return CP.intrinsic_forces(self.parts, pos, self.shape, self.p.walls)
 
-    def _couple(self, v, u, Fint, s, include_int=True):
+    def _couple(self, v, u, Fint, s, include_int=True, sub=0):
+        """F^h of coupling (sub-)step number `sub` of the current step (its
+        random force when thermal: FC and original EBF)."""
         c = self.cpl
+        zeta = None
+        if self.kT > 0.0 and c.kind in ('fc', 'ebf'):
+            gam = self.p.rho0 if c.kind == 'ebf' else c.gamma
+            zeta = fluct.particle_noise(len(v), self._tnow, sub, s, gam, self.kT, self.seed)
         return CP.coupling_force(c.kind, c.order, v, u, Fint, self.parts.mass,
-                                 s, c.gamma, self.p.rho0, include_int)
+                                 s, c.gamma, self.p.rho0, include_int, zeta)
 
     # ------------------------------------------------------------- steps
     def step(self):
         c = self.cpl
+        self._tnow = self.tstep          # the thermal counter of this step
         if c.kind == 'none' or self.parts is None:
             self._step_fluid_only()
         elif c.kind == 'ibm':
@@ -134,7 +171,7 @@ class Sim:
 
     def _step_fluid_only(self):
         if self.cpl.order == 1:
-            self.fbar = lb.step_first_order(self.fbar, None, self.p)
+            self.fbar = self._lb(None, None)
             return
         zero = np.zeros((3,) + self.shape)
         self.fbar = self._lb(zero, zero)
@@ -146,12 +183,12 @@ class Sim:
         r = self._wrap(P.pos + 0.5 * P.vel)
         Fint = self._fint(r)
         u = self._interp(self._fluid_velocity(self.Fa, g), r)
-        Fh = self._couple(P.vel, u, Fint, 0.5)
+        Fh = self._couple(P.vel, u, Fint, 0.5, sub=0)
         v = P.vel + (0.5 / P.mass[:, None]) * (Fh + Fint)
         Fb = self._spread(-Fh, r)
         self.fbar = self._lb(self.Fa, Fb)
         u = self._interp(self._fluid_velocity(), r)
-        Fh = self._couple(v, u, Fint, 0.5)
+        Fh = self._couple(v, u, Fint, 0.5, sub=1)
         self.Fa = self._spread(-Fh, r)
         v = v + (0.5 / P.mass[:, None]) * (Fh + Fint)
         P.pos = self._wrap(r + 0.5 * v)
@@ -174,7 +211,7 @@ class Sim:
             else:
                 field = self._fluid_velocity(acc, (s / n) * g)
             u = self._interp(field, r)
-            Fh = self._couple(v, u, Fint, dt)
+            Fh = self._couple(v, u, Fint, dt, sub=(0 if before else n) + s)
             v = v + (dt / P.mass[:, None]) * (Fh + Fint)
             acc = acc + (1.0 / n) * self._spread(-Fh, r)
             r = self._wrap(r + 0.5 * dt * v)
@@ -205,14 +242,14 @@ class Sim:
         r, v = P.pos, P.vel
         zero = np.zeros_like(v)
         u = self._interp(self._fluid_velocity(self.Fa, g), r)
-        Fh = self._couple(v, u, zero, 0.5, include_int=False)
+        Fh = self._couple(v, u, zero, 0.5, include_int=False, sub=0)
         v = v + (0.5 / P.mass[:, None]) * Fh
         Fb = self._spread(-Fh, r)
         r, v = self._verlet_int(r, v)
         self.fbar = self._lb(self.Fa, Fb)
         r, v = self._verlet_int(r, v)
         u = self._interp(self._fluid_velocity(), r)
-        Fh = self._couple(v, u, zero, 0.5, include_int=False)
+        Fh = self._couple(v, u, zero, 0.5, include_int=False, sub=1)
         self.Fa = self._spread(-Fh, r)
         v = v + (0.5 / P.mass[:, None]) * Fh
         P.pos, P.vel = r, v
@@ -223,10 +260,10 @@ class Sim:
         r = P.pos
         Fint = self._fint(r)
         u = self._interp(self._fluid_velocity(), r)
-        Fh = self._couple(P.vel, u, Fint, 1.0)
+        Fh = self._couple(P.vel, u, Fint, 1.0, sub=0)
         v = P.vel + (1.0 / P.mass[:, None]) * (Fh + Fint)
         F = self._spread(-Fh, r)
-        self.fbar = lb.step_first_order(self.fbar, F, self.p)
+        self.fbar = self._lb(None, F)
         P.pos = self._wrap(r + v)
         P.vel = v
         self.last_Fh = Fh
@@ -250,7 +287,7 @@ class Sim:
         P = self.parts
         X = P.pos
         F = self._fint(X)
-        self.fbar = lb.step_first_order(self.fbar, self._spread(F, X), self.p)
+        self.fbar = self._lb(None, self._spread(F, X))
         u1 = self._fluid_velocity()
         P.pos = self._wrap(X + self._interp(u1, X))
         self.last_Fh = F

@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbc.so")
 
-SOURCES = ["lb_kernels.cu", "particle_kernels.cu", "lbc_api.cu", "noalloc.cu", "lb_fluct.cu"]
+SOURCES = ["lb_kernels.cu", "particle_kernels.cu", "lbc_api.cu", "noalloc.cu", "lb_thermal.cu",
+           "lb_stress.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -73,7 +73,8 @@ struct Layout {
   size_t off_rb_first, off_rb_count, off_rb_radius, off_rb_body_of, off_rb_ref, off_rb_frames,
       off_rb_frep;
   size_t off_red, off_redout;
-  size_t off_thermal;                // step counter of the thermal fluctuations
+  size_t off_thermal;                // two slots of the thermal step counter (by step parity)
+  size_t off_health;                 // health word set by the LB steps (non-finite density)
   int ntiles, maxnt;
   bool has_particles;
   bool use_ncache;
@@ -159,7 +160,8 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
   }
   L.off_red = take((size_t)invariants_blocks(g) * 5 * sizeof(double));
   L.off_redout = take(16 * sizeof(double));
-  L.off_thermal = take(sizeof(unsigned long long));
+  L.off_thermal = take(2 * sizeof(unsigned long long));
+  L.off_health = take(sizeof(int));
   L.total = o;
   return L;
 }
@@ -201,7 +203,14 @@ struct lbc_box {
   bool mom_on;         // gathers read the node-moment field (LBC_OPT_NODE_MOMENTS)
   int gather_lanes;    // LBC_OPT_GATHER_LANES
   bool thermal;        // LB steps with thermal fluctuations (lbc_box_set_thermal)
-  FluctArgs fl;        // their amplitudes and Philox key
+  double kT;           // their temperature k_B T
+  uint64_t seed;       // and Philox key; the step counter restarts when it changes
+  bool seeded;         // a seed has been given (the counter runs from then on)
+  bool tstep_reset;    // zero the counter slots before the next step
+  int printed_amp;     // LBC_OPT_THERMAL_AMPLITUDE: 1 = the amplitude as printed
+  int tlast;           // the counter slot holding the latest count
+  Real psi[Q];         // kick amplitudes of the fluid moments
+  void* sigma;         // stress output of every LB step (lbc_box_set_stress_output), or null
   // device pointers
   void* pop(int k) { return arena + L.off_pop[k]; }
   void* F(int k) { return L.has_particles ? static_cast<void*>(arena + L.off_F[k]) : nullptr; }
@@ -257,8 +266,25 @@ void fill_lb_args(lbc_box* b) {
     a.bb_bot[i] = make_real(l.z_walls ? 6.0 * w * l.rho0 * cu_b : 0.0);
     a.bb_top[i] = make_real(l.z_walls ? 6.0 * w * l.rho0 * cu_t : 0.0);
   }
+  a.health = reinterpret_cast<int*>(b->arena + b->L.off_health);
   a.scale16 = (float)(l.storage_scale != 0.0 ? l.storage_scale : 1.0);
   a.rscale16 = (float)(1.0 / (l.storage_scale != 0.0 ? l.storage_scale : 1.0));
+}
+
+// slot k of the thermal step counter (a step at buffer parity k reads slot k
+// and writes slot 1 - k)
+unsigned long long* tstep_slot(lbc_box* b, int k) {
+  return reinterpret_cast<unsigned long long*>(b->arena + b->L.off_thermal) + k;
+}
+
+// thermal arguments of an LB step that starts at buffer parity par
+void thermal_args(lbc_box* b, LBArgs& a, int par) {
+  a.thermal = 1;
+  for (int i = 0; i < Q; ++i) a.psi[i] = b->psi[i];
+  a.tkey0 = (uint32_t)(b->seed & 0xFFFFFFFFu);
+  a.tkey1 = (uint32_t)(b->seed >> 32);
+  a.tstep = tstep_slot(b, par);
+  a.tstep_next = tstep_slot(b, 1 - par);
 }
 
 bool order2(const lbc_box* b) { return b->cpl.order == 2; }
@@ -308,6 +334,11 @@ struct Plan {
 
   void lb(const void* Fa, const void* Fb, double ca, double cb, double cg) {
     LBArgs a = b->lb;
+    if (b->thermal) {
+      thermal_args(b, a, b->cur);
+      b->tlast = 1 - b->cur;          // the slot this step leaves the count in
+    }
+    a.sigma = b->sigma;
     a.Fa = Fa; a.flag_a = Fa ? (Fa == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.Fb = Fb; a.flag_b = Fb ? (Fb == b->F(0) ? b->flag(0) : b->flag(1)) : nullptr;
     a.ca = make_real(ca); a.cb = make_real(cb);
@@ -339,13 +370,12 @@ struct Plan {
     // graph (external events), not capture-internal dependencies
     const unsigned rf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (e0) cudaEventRecordWithFlags(e0, s, rf);
-    if (b->thermal) {
-      launch_lb_fluct(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, b->fl,
-                      reinterpret_cast<unsigned long long*>(b->arena + b->L.off_thermal), s);
-      ++n;                 // the step counter's advance
-    } else {
+    if (b->thermal)
+      launch_lb_thermal(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
+    else if (b->sigma)
+      launch_lb_stress(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
+    else
       launch_lb_step(b->lat.storage, b->pop(b->cur), b->pop(1 - b->cur), a, s);
-    }
     if (e1) cudaEventRecordWithFlags(e1, s, rf);
     b->cur = 1 - b->cur;
     ++n;
@@ -487,6 +517,20 @@ struct Plan {
     for (int c = 0; c < 3; ++c) a.cgg[c] = make_real(cg * b->lat.body_force[c]);
   }
 
+  // the random force of a force-coupled (sub-)step `sub` of length s
+  // (thermal boxes; FC and original EBF: the modified EBF's no-slip
+  // condition determines F^h entirely, so it carries none)
+  void noise(GatherArgs& a, int sub, double s) {
+    if (!b->thermal || (b->cpl.kind != LBC_FC && b->cpl.kind != LBC_EBF)) return;
+    const double gam = b->cpl.kind == LBC_EBF ? b->lat.rho0 : b->cpl.gamma;
+    a.noise = 1;
+    a.substep = sub;
+    a.zeta_amp = make_real(std::sqrt(2.0 * b->kT * gam / s));
+    a.tkey0 = (uint32_t)(b->seed & 0xFFFFFFFFu);
+    a.tkey1 = (uint32_t)(b->seed >> 32);
+    a.tstep = tstep_slot(b, par);
+  }
+
   void gather(const GatherArgs& a) {
     if (!on()) return;
     launch_gather(part_args(b), a, s);
@@ -583,6 +627,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     GatherArgs a = P.gather_base();
     a.mode = GM_COUPLE; a.s = make_real(h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
+    P.noise(a, 0, h);
     P.gather(a);
     P.spread(ib, false);
     P.lb(nullptr, b->F(ib), 0.0, h, h);
@@ -598,12 +643,14 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     GatherArgs a = P.gather_base();
     a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
+    P.noise(a, 0, 0.5 * h);
     P.gather(a);
     P.spread(ib, false);
     P.lb(b->F(ia), b->F(ib), 0.5 * h, 0.5 * h, h);
     a = P.gather_base();
     a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 1; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
+    P.noise(a, 1, 0.5 * h);
     P.gather(a);
     P.spread(ia, false);
     P.drift(0.5 * h, 0.0, 0.0, false, false);
@@ -645,6 +692,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
           P.fields(a, ia, 0.5 * h, k > 0 ? ib : -1, 0.5 * h, 0.5 * h + gfrac);
         else
           P.fields(a, -1, 0.0, k > 0 ? ia : -1, 0.5 * h, gfrac);
+        P.noise(a, half * n + k, dt);
         P.gather(a);
         P.spread(out, k > 0);
       }
@@ -663,6 +711,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     GatherArgs a = P.gather_base();
     a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 0; a.rec_weight = make_real(1.0);
     P.fields(a, ia, 0.5 * h, -1, 0.0, 0.5 * h);
+    P.noise(a, 0, 0.5 * h);
     P.gather(a);
     P.spread(ib, false);
     for (int k = 0; k < n; ++k) P.drift(0.5 * dt, dt, 0.5 * dt, true, false);
@@ -672,14 +721,54 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     a = P.gather_base();
     a.mode = GM_COUPLE; a.s = make_real(0.5 * h); a.include_int = 0; a.rec_weight = make_real(1.0);
     P.fields(a, -1, 0.0, -1, 0.0, 0.0);
+    P.noise(a, 1, 0.5 * h);
     P.gather(a);
     P.spread(ia, false);
   }
   *launches += P.n;
 }
 
+// Before a run of steps, outside any capture: zero the thermal step counter
+// after a seed change, and carry the latest count into the slot the next
+// step reads (plain steps in between flip the buffers without advancing it).
+lbc_status thermal_prepare(lbc_box* b, cudaStream_t s) {
+  if (b->tstep_reset) {
+    CK(cudaMemsetAsync(tstep_slot(b, 0), 0, 2 * sizeof(unsigned long long), s));
+    b->tstep_reset = false;
+    b->tlast = b->cur;
+  }
+  if (b->thermal && b->tlast != b->cur) {
+    CK(cudaMemcpyAsync(tstep_slot(b, b->cur), tstep_slot(b, b->tlast), sizeof(unsigned long long),
+                       cudaMemcpyDeviceToDevice, s));
+    b->tlast = b->cur;
+  }
+  return LBC_OK;
+}
+
+// kick amplitudes psi_k = phi_k / b_k of the fluid moments at the box's k_B T
+void thermal_amplitudes(lbc_box* b) {
+  const bool mrt = b->lat.collision == LBC_MRT;
+  double gk[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int q = 1; q < 5; ++q) gk[q] = mrt ? b->lb.gamma_k[q - 1].d : b->lb.gamma_bgk.d;
+  const double mu = b->kT / (1.0 / 3.0);          // k_B T / (a^3 cs2), a = 1
+  for (int k = 0; k < Q; ++k) {
+    if (k < 4) {
+      b->psi[k] = make_real(0.0);
+      continue;
+    }
+    const double gam = gk[mrt_group(k)], lam = 1.0 - gam;
+    const double bk = mrt_b(k);
+    const double var = b->printed_amp ? mu * bk * lam * lam : mu * bk * (1.0 - gam * gam);
+    b->psi[k] = make_real(std::sqrt(var) / bk);
+  }
+}
+
 lbc_status run_steps(lbc_box* b, int64_t nsteps, cudaStream_t s) {
   int64_t dummy = 0;
+  {
+    const lbc_status st = thermal_prepare(b, s);
+    if (st != LBC_OK) return st;
+  }
   while (nsteps > 0 && (!b->steady || !b->use_graphs || nsteps < 2)) {
     int64_t l = 0;
     enqueue_step(b, s, &l);
@@ -799,6 +888,9 @@ void moments_stale(lbc_box* b, cudaStream_t s) {
 // the populations were replaced from outside a step: node moments cached
 // for the next step's first half are stale
 void populations_changed(lbc_box* b, cudaStream_t s) {
+  // a new state: the health word and a latched non-finite status start over
+  cudaMemsetAsync(b->arena + b->L.off_health, 0, sizeof(int), s);
+  if (b->status == LBC_ERR_NONFINITE) b->status = LBC_OK;
   if (!b->L.has_particles) return;
   int* f = b->iptr(b->L.off_sortflags);
   cudaMemsetAsync(f + 1, 1, sizeof(int), s);
@@ -953,7 +1045,14 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
   b->mom_on = L.has_particles && L.has_mom && moments_pay(L, b->cpl, max_particles);
   b->gather_lanes = 0;
   b->thermal = false;
-  std::memset(&b->fl, 0, sizeof(b->fl));
+  b->kT = 0.0;
+  b->seed = 0;
+  b->seeded = false;
+  b->tstep_reset = false;
+  b->printed_amp = 0;
+  b->tlast = 0;
+  for (int i = 0; i < Q; ++i) b->psi[i] = make_real(0.0);
+  b->sigma = nullptr;
   fill_lb_args(b);
   cudaStream_t s = S(stream);
   if (L.has_particles) {
@@ -972,6 +1071,10 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
     }
   }
   lbc_status st = clear_pending(b, s);
+  if (st == LBC_OK && (cudaMemset(b->arena + L.off_thermal, 0, 2 * sizeof(unsigned long long)) !=
+                           cudaSuccess ||
+                       cudaMemset(b->arena + L.off_health, 0, sizeof(int)) != cudaSuccess))
+    st = LBC_ERR_CUDA;
   if (st == LBC_OK) {
     const double u0[3] = {0.0, 0.0, 0.0};
     st = lbc_box_init_equilibrium(b, lat->rho0, u0, stream);
@@ -1306,8 +1409,9 @@ lbc_status lbc_box_invariants(lbc_box* b, double* mass, double* momentum, void* 
   const bool pm = particles(b) && b->cpl.kind != LBC_IBM;
   if (pm) launch_particle_momentum(b->M, b->dptr(b->L.off_vel[b->pc]), b->dptr(b->L.off_mass), out + 8, s);
   double h[16] = {0};
-  int drift_flag = 0;
+  int drift_flag = 0, health = 0;
   CK(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&health, b->arena + b->L.off_health, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (b->L.has_particles)
     CK(cudaMemcpyAsync(&drift_flag, b->iptr(b->L.off_status), sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1318,7 +1422,20 @@ lbc_status lbc_box_invariants(lbc_box* b, double* mass, double* momentum, void* 
   if (mass) *mass = (double)g.nx * g.ny * g.nz * b->lat.rho0 + h[0];
   if (momentum)
     for (int c = 0; c < 3; ++c) momentum[c] = h[1 + c] + (pm ? h[8 + c] : 0.0);
-  if (h[4] != 0.0 && b->status == LBC_OK) b->status = LBC_ERR_NONFINITE;
+  if ((h[4] != 0.0 || (health & 1)) && b->status == LBC_OK) b->status = LBC_ERR_NONFINITE;
+  return b->status;
+}
+
+lbc_status lbc_box_check(lbc_box* b, void* stream) {
+  if (!b) return LBC_ERR_ARG;
+  cudaStream_t s = S(stream);
+  int health = 0, drift_flag = 0;
+  CK(cudaMemcpyAsync(&health, b->arena + b->L.off_health, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (b->L.has_particles)
+    CK(cudaMemcpyAsync(&drift_flag, b->iptr(b->L.off_status), sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if ((health & 1) && b->status == LBC_OK) b->status = LBC_ERR_NONFINITE;
+  if (drift_flag && b->status == LBC_OK) b->status = LBC_ERR_STATE;
   return b->status;
 }
 
@@ -1366,6 +1483,13 @@ lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
     b->gather_lanes = (int)value;
     return LBC_OK;
   }
+  if (option == LBC_OPT_THERMAL_AMPLITUDE) {
+    if (value != 0 && value != 1) return LBC_ERR_ARG;
+    reset_graphs(b);
+    b->printed_amp = (int)value;
+    if (b->thermal) thermal_amplitudes(b);
+    return LBC_OK;
+  }
   return LBC_ERR_ARG;
 }
 
@@ -1375,6 +1499,7 @@ lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) 
   else if (option == LBC_OPT_TIMING) *value = b->timing_cap;
   else if (option == LBC_OPT_NODE_MOMENTS) *value = b->mom_on ? 1 : 0;
   else if (option == LBC_OPT_GATHER_LANES) *value = b->gather_lanes;
+  else if (option == LBC_OPT_THERMAL_AMPLITUDE) *value = b->printed_amp;
   else return LBC_ERR_ARG;
   return LBC_OK;
 }
@@ -1382,29 +1507,33 @@ lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) 
 lbc_status lbc_box_set_thermal(lbc_box* b, double kT, uint64_t seed) {
   if (!b || !(kT >= 0.0) || !std::isfinite(kT)) return LBC_ERR_ARG;
   if (b->batch) return LBC_ERR_STATE;
-  const int st = b->lat.storage;
-  if (kT > 0.0 && st != LBC_F32 && st != LBC_F64) return LBC_ERR_STATE;
+  if (kT > 0.0 && (b->sigma || (long long)Q * b->L.g.qstride >= (1LL << 31)))
+    return LBC_ERR_UNSUPPORTED;
   reset_graphs(b);
   b->thermal = kT > 0.0;
-  std::memset(&b->fl, 0, sizeof(b->fl));
+  b->kT = kT;
   if (!b->thermal) return LBC_OK;
-  // eigenvalues 1 - lambda per relaxation group (BGK: one for all)
-  const bool mrt = b->lat.collision == LBC_MRT;
-  double gk[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int q = 1; q < 5; ++q) gk[q] = mrt ? b->lb.gamma_k[q - 1].d : b->lb.gamma_bgk.d;
-  for (int q = 0; q < 5; ++q) b->fl.gk[q] = make_real(gk[q]);
-  const double mu = kT / (1.0 / 3.0);          // k_B T / (a^3 cs2), a = 1
-  for (int k = 4; k < Q; ++k) {
-    const double gam = gk[mrt_group(k)];
-    const double bk = mrt_b(k);
-    b->fl.psi[k] = make_real(std::sqrt(mu * bk * (1.0 - gam * gam)) / bk);
+  if (!b->seeded || seed != b->seed) {      // a new sequence: the counter restarts
+    b->seed = seed;
+    b->seeded = true;
+    b->tstep_reset = true;
   }
-  b->fl.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
-  b->fl.key1 = (uint32_t)(seed >> 32);
-  b->fl.step = reinterpret_cast<const unsigned long long*>(b->arena + b->L.off_thermal);
-  CK(cudaDeviceSynchronize());
-  CK(cudaMemset(b->arena + b->L.off_thermal, 0, sizeof(unsigned long long)));
-  CK(cudaDeviceSynchronize());
+  thermal_amplitudes(b);
+  return LBC_OK;
+}
+
+lbc_status lbc_box_set_stress_output(lbc_box* b, void* sigma_dev, size_t bytes) {
+  if (!b) return LBC_ERR_ARG;
+  if (b->batch) return LBC_ERR_STATE;
+  if (sigma_dev) {
+    const size_t need = 6 * (size_t)b->L.g.nx * b->L.g.ny * b->L.g.nz *
+                        (b->lat.storage == LBC_F64 ? sizeof(double) : sizeof(float));
+    if (reinterpret_cast<uintptr_t>(sigma_dev) & 15u) return LBC_ERR_ARG;
+    if (bytes < need) return LBC_ERR_OOM;
+    if (b->thermal || (long long)Q * b->L.g.qstride >= (1LL << 31)) return LBC_ERR_UNSUPPORTED;
+  }
+  reset_graphs(b);
+  b->sigma = sigma_dev;
   return LBC_OK;
 }
 
@@ -1539,6 +1668,12 @@ struct lbc_batch {
   int parity;        // toggled every batched step
   bool steady;       // a batched step ran since the membership last changed
   int64_t launches;  // kernel launches of one batched step
+  // members' health words after the last advance, copied to pinned host
+  // memory behind health_ev and read at the next advance without waiting
+  int* hhealth;
+  std::vector<lbc_box*> hboxes;   // the member of each copied word
+  cudaEvent_t health_ev;
+  bool health_pending;
 };
 
 namespace {
@@ -1580,9 +1715,10 @@ lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vecto
   }
   // group the recorded LB steps; rows are numbered per group in table order
   struct Key {
-    int storage, coll, walls, forced;
+    int storage, coll, walls, forced, thermal;
     bool operator==(const Key& o) const {
-      return storage == o.storage && coll == o.coll && walls == o.walls && forced == o.forced;
+      return storage == o.storage && coll == o.coll && walls == o.walls && forced == o.forced &&
+             thermal == o.thermal;
     }
   };
   std::vector<Key> keys;
@@ -1591,7 +1727,7 @@ lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vecto
     const lbc_box* b = B->members[j].box;
     const BoxEntry& e = b->deferred;
     const Key k{b->lat.storage, lb_collision_variant(e.a), e.a.g.walls,
-                (e.a.Fa != nullptr || e.a.Fb != nullptr) ? 1 : 0};
+                (e.a.Fa != nullptr || e.a.Fb != nullptr) ? 1 : 0, e.a.thermal ? 1 : 0};
     size_t gi = 0;
     while (gi < keys.size() && !(keys[gi] == k)) ++gi;
     if (gi == keys.size()) { keys.push_back(k); groups.emplace_back(); }
@@ -1613,8 +1749,14 @@ lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vecto
   if (copy && !host.empty())
     CK(cudaMemcpyAsync(dev, host.data(), host.size() * sizeof(BoxEntry), cudaMemcpyHostToDevice, main));
   for (size_t gi = 0; gi < groups.size(); ++gi) {
-    launch_lb_batch(keys[gi].storage, dev + spans[gi].first, (int)groups[gi].size(),
-                    spans[gi].second, keys[gi].coll, keys[gi].walls != 0, keys[gi].forced != 0, main);
+    if (keys[gi].thermal)
+      launch_lb_batch_thermal(keys[gi].storage, dev + spans[gi].first, (int)groups[gi].size(),
+                              spans[gi].second, keys[gi].coll, keys[gi].walls != 0,
+                              keys[gi].forced != 0, main);
+    else
+      launch_lb_batch(keys[gi].storage, dev + spans[gi].first, (int)groups[gi].size(),
+                      spans[gi].second, keys[gi].coll, keys[gi].walls != 0, keys[gi].forced != 0,
+                      main);
     ++l;
   }
   CK(cudaEventRecord(B->fork[1], main));
@@ -1700,7 +1842,14 @@ int batch_find(const lbc_batch* B, const lbc_box* b) {
   return -1;
 }
 
+// forget the copied health word of a box that leaves (or joins) the batch
+void batch_forget(lbc_batch* B, const lbc_box* b) {
+  for (auto& p : B->hboxes)
+    if (p == b) p = nullptr;
+}
+
 void batch_drop(lbc_batch* B, int j) {
+  batch_forget(B, B->members[j].box);
   B->members[j].box->batch = nullptr;
   B->members.erase(B->members.begin() + j);
   batch_reset_graphs(B);
@@ -1740,9 +1889,15 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
     B->fork[k] = nullptr;
   }
   B->done_ev = nullptr;
+  B->hhealth = nullptr;
+  B->health_ev = nullptr;
+  B->health_pending = false;
   bool ok = cudaEventCreateWithFlags(&B->fork[0], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&B->fork[1], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->health_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaHostAlloc(reinterpret_cast<void**>(&B->hhealth), (size_t)max_boxes * sizeof(int),
+                          cudaHostAllocDefault) == cudaSuccess;
   B->streams.assign(max_boxes, nullptr);
   B->events.assign(max_boxes, nullptr);
   for (int j = 0; ok && j < max_boxes; ++j)
@@ -1759,9 +1914,10 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
 lbc_status lbc_batch_add(lbc_batch* B, lbc_box* b, int64_t steps) {
   if (!B || !b || steps < 1) return LBC_ERR_ARG;
   if (b->L.g.nx > LBC_BATCH_MAX_NX) return LBC_ERR_ARG;
-  if (b->batch != nullptr || b->timing_cap > 0 || b->thermal) return LBC_ERR_STATE;
+  if (b->batch != nullptr || b->timing_cap > 0 || b->sigma) return LBC_ERR_STATE;
   if ((int)B->members.size() >= B->max_boxes) return LBC_ERR_OOM;
   if (b->status != LBC_OK) return b->status;
+  batch_forget(B, b);
   B->members.push_back({b, steps, false});
   b->batch = B;
   batch_reset_graphs(B);
@@ -1789,12 +1945,37 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
   if (!B || max_steps < 0 || !nfinished || !steps_done) return LBC_ERR_ARG;
   *nfinished = 0;
   *steps_done = 0;
+  // health words of the previous advance, if their copies are done (no
+  // wait): a member whose steps met a non-finite density is latched failed
+  if (B->health_pending) {
+    const cudaError_t q = cudaEventQuery(B->health_ev);
+    if (q == cudaSuccess) {
+      for (auto& m : B->members)
+        for (size_t j = 0; j < B->hboxes.size(); ++j)
+          if (B->hboxes[j] == m.box && (B->hhealth[j] & 1) && m.box->status == LBC_OK)
+            m.box->status = LBC_ERR_NONFINITE;
+      B->health_pending = false;
+    } else if (q == cudaErrorNotReady) {
+      cudaGetLastError();           // not an error: the copies are still in flight
+    } else {
+      return LBC_ERR_CUDA;
+    }
+  }
+  // failed members leave the batch (reported as finished: their status says
+  // why) and the others go on
+  for (int j = (int)B->members.size() - 1; j >= 0; --j) {
+    if (B->members[j].box->status == LBC_OK) continue;
+    if (finished) finished[*nfinished] = B->members[j].box;
+    ++*nfinished;
+    batch_drop(B, j);
+  }
   if (B->members.empty() || max_steps == 0) return LBC_OK;
   cudaStream_t s = S(stream);
   int64_t k = max_steps;
   for (const auto& m : B->members) {
-    if (m.box->status != LBC_OK) return m.box->status;
     if (m.remaining < k) k = m.remaining;
+    const lbc_status st = thermal_prepare(m.box, s);
+    if (st != LBC_OK) return st;
   }
   std::vector<BoxEntry> host;
   int64_t done = 0;
@@ -1822,6 +2003,16 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
     }
   }
   CK(cudaEventRecord(B->done_ev, s));
+  // the members' health words, read by the next advance
+  B->hboxes.clear();
+  for (size_t j = 0; j < B->members.size(); ++j) {
+    lbc_box* b = B->members[j].box;
+    B->hboxes.push_back(b);
+    CK(cudaMemcpyAsync(B->hhealth + j, b->arena + b->L.off_health, sizeof(int),
+                       cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaEventRecord(B->health_ev, s));
+  B->health_pending = true;
   for (auto& m : B->members) m.remaining -= k;
   for (int j = (int)B->members.size() - 1; j >= 0; --j) {
     if (B->members[j].remaining > 0) continue;
@@ -1845,6 +2036,11 @@ lbc_status lbc_batch_destroy(lbc_batch* B) {
   for (int k = 0; k < 2; ++k)
     if (B->fork[k]) cudaEventDestroy(B->fork[k]);
   if (B->done_ev) cudaEventDestroy(B->done_ev);
+  if (B->health_ev) {
+    if (B->health_pending) cudaEventSynchronize(B->health_ev);   // copies into hhealth
+    cudaEventDestroy(B->health_ev);
+  }
+  if (B->hhealth) cudaFreeHost(B->hhealth);
   for (cudaStream_t st : B->streams)
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t ev : B->events)

@@ -31,26 +31,34 @@ struct LBArgs {
   int block_x, block_y;   // LB launch shape (0: default rows of up to 256 cells)
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
   float rscale16;         // 1 / scale16
+  // Thermal fluctuations (Eq. [mrt-fluct]), thermal != 0: the
+  // non-equilibrium part of every moment k >= 4 (normalised moments
+  // (sum_i e_ki v_i) / b_k) receives psi_k sqrt(rho) r_k after its
+  // relaxation, r_k standard normal from Philox4x32-10 with counter
+  // (flat cell, step, 0, k / 4) and key (tkey0, tkey1).  The step is read
+  // from *tstep; the step writes *tstep + 1 to *tstep_next (the slot the
+  // next step reads: two slots alternate with the population buffers).
+  int thermal;
+  Real psi[Q];
+  uint32_t tkey0, tkey1;
+  const unsigned long long* tstep;
+  unsigned long long* tstep_next;
+  // health word of the box: bit 0 is set by any step that meets a
+  // non-finite density (NaN anywhere in a cell's populations reaches rho)
+  int* health;
+  // viscous stress of the collided populations (Eq. [viscstress]), written
+  // by the stress variant of the step when not null: dense
+  // [6][nz][ny][nx] in the compute type, components xx, yy, zz, xy, yz, xz
+  void* sigma;
 };
 
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,
                     cudaStream_t s);
-
-// Thermal fluctuations of the LB step (Eq. [mrt-fluct]): the non-equilibrium
-// part of moment k (4..18) relaxes by gk[group of k] and is kicked by
-// psi_k sqrt(rho) r_k, psi_k = phi_k / b_k in the normalised moments
-// (sum_i e_ki v_i) / b_k, r_k standard normal from Philox4x32-10 with counter
-// (cell, step, 0, k / 4) and key (key0, key1); step is read from *step.
-struct FluctArgs {
-  Real gk[5];                         // per relaxation group (group 0 unused)
-  Real psi[Q];
-  uint32_t key0, key1;
-  const unsigned long long* step;
-};
-// the fluctuating LB step (FP32 / FP64 storage), then the step counter
-// advanced by one
-void launch_lb_fluct(int storage, const void* fin, void* fout, const LBArgs& a,
-                     const FluctArgs& t, unsigned long long* step, cudaStream_t s);
+// the fused step with thermal fluctuations (lb_thermal.cu) or with the
+// stress epilogue (lb_stress.cu; a.sigma must be set); both return false,
+// launching nothing, for arrays of 2^31 or more elements (32-bit indices)
+bool launch_lb_thermal(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s);
+bool launch_lb_stress(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s);
 
 // One entry of a batched LB launch: a box's arguments, its source and
 // destination population arrays, and its first row in the launch (rows =
@@ -63,9 +71,12 @@ struct BoxEntry {
 };
 // 0 BGK, 1 general MRT, 2 MRT with fully relaxed ghosts
 int lb_collision_variant(const LBArgs& a);
-// all boxes of one launch share storage, collision variant, walls and forcing
+// all boxes of one launch share storage, collision variant, walls, forcing
+// and the thermal flag (thermal groups take the second launch)
 void launch_lb_batch(int storage, const BoxEntry* boxes, int nboxes, long long rows, int coll,
                      bool walls, bool forced, cudaStream_t s);
+void launch_lb_batch_thermal(int storage, const BoxEntry* boxes, int nboxes, long long rows,
+                             int coll, bool walls, bool forced, cudaStream_t s);
 // fbar (post-streaming deviations) -> stored pre-streaming form, and back
 void launch_unstream(int storage, const void* fbar, void* fstar, const LBArgs& a,
                      cudaStream_t s);
@@ -238,6 +249,15 @@ struct GatherArgs {
   uint32_t* mark;
   int4* live_tiles;               // (tile, tx, ty, tz)
   int* nlive;
+  // random force zeta of the force coupling (Sec. 5.2, Eq. [modified-force])
+  // when noise != 0: three standard normals from Philox4x32-10 with counter
+  // (particle index, step, 8 + substep, 0) and key (tkey0, tkey1), scaled
+  // by zeta_amp = sqrt(2 k_B T gamma / s), the step read from *tstep
+  int noise;
+  int substep;
+  Real zeta_amp;
+  uint32_t tkey0, tkey1;
+  const unsigned long long* tstep;
 };
 void launch_gather(const PartArgs& p, const GatherArgs& a, cudaStream_t s);
 // Node-moment field.  Bricks are 32 x 4 x 4 cells (eight tiles along x),

@@ -3,11 +3,10 @@
 // and without caller-provided scratch.
 //
 // Some callers cannot call cudaMalloc (or hand the library a scratch arena):
-// code that runs while a CUDA graph is being captured, where an allocation
-// would break the capture; processes whose device memory is fully reserved
-// by a memory pool or another framework; and lightweight monitoring hooks
-// that only hold a pointer to someone else's buffer.  This entry point keeps
-// its per-plane partial sums in a fixed file-scope device array instead.
+// processes whose device memory is fully reserved by a memory pool or another
+// framework, and lightweight monitoring hooks that only hold a pointer to
+// someone else's buffer.  This entry point keeps its per-plane partial sums
+// in a fixed file-scope device array instead.
 //
 // The scratch is shared by every call in the process on a given device and
 // keeps the previous call's partial sums; each call overwrites all the slots
@@ -79,7 +78,9 @@ total_kernel(const double* sums, int nz, double* out) {
 }
 
 // Device address of the scratch for the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The address belongs to the
+// device's context at the time of the lookup: the library is not to be used
+// across a device reset (the header says so).
 lbc_status scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBC_ERR_CUDA;

@@ -27,8 +27,25 @@
 // any lattice-Boltzmann regime).  The interpolation kernel checks this and
 // raises a status flag if it is violated.
 #include "lb_device.cuh"
+#include "philox.cuh"
 
 namespace lbc {
+
+// ------------------------------------------------------------ launch caches
+// Launch quantities that depend on the device (SM count, occupancy) are
+// cached per device ordinal, so one process may drive GPUs of different
+// sizes.
+constexpr int MAX_DEVICES = 64;
+inline int device_slot(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) dev = 0;
+  if (sms) {
+    *sms = 0;
+    cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    if (*sms <= 0) *sms = 1;
+  }
+  return dev;
+}
 
 // ------------------------------------------------------------ 1-D stencils
 // phi_4 (Peskin): (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8 on |r| <= 1,
@@ -709,12 +726,13 @@ void launch_small_sort_bins(long long M, int key_bits, const uint32_t* kin, cons
                             uint32_t* home, const int* need, int* changed, int* brick_count,
                             cudaStream_t s) {
   if (M <= 0) return;
-  static bool attr = false;
+  static bool attr[MAX_DEVICES] = {false};
   const size_t smem = (size_t)16 * (size_t)M;
-  if (!attr) {
+  const int dev = device_slot(nullptr);
+  if (!attr[dev]) {
     cudaFuncSetAttribute(small_sort_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(16 * SMALL_SORT_MAX));
-    attr = true;
+    attr[dev] = true;
   }
   small_sort_bins_kernel<<<1, SMALL_SORT_THREADS, smem, s>>>((int)M, key_bits, kin, vin, ka, va,
                                                              ntiles, tb, te, home, need, changed,
@@ -1042,12 +1060,26 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
         for (int c = 0; c < 3; ++c) Fh[c] = -dv[c] * inv - r * Fi[c];
       } else {
         const C gam = a.kind == 3 ? crho : rv<C>(a.gamma);   // EBF: rho a^3 / h
+        // the random force zeta of this (sub-)step (thermal boxes)
+        C zeta[3] = {C(0), C(0), C(0)};
+        if (a.noise) {
+          C r[4];
+          philox_gauss4<C>((uint32_t)i, (uint32_t)(*a.tstep), 8u + (uint32_t)a.substep, 0u,
+                           a.tkey0, a.tkey1, r);
+          const C za = rv<C>(a.zeta_amp);
+          for (int c = 0; c < 3; ++c) zeta[c] = za * r[c];
+        }
         if (a.order == 1) {
           for (int c = 0; c < 3; ++c) Fh[c] = -gam * dv[c];
+          if (a.noise)
+            for (int c = 0; c < 3; ++c) Fh[c] += zeta[c];
         } else {                              // Crank-Nicolson, Eq. [modified-force]
           const C al = gam * cs * cim, be = gam * cs / crho;
           const C D = C(1) + C(0.5) * al + C(0.5) * be;
-          for (int c = 0; c < 3; ++c) Fh[c] = -(gam * dv[c] + C(0.5) * al * Fi[c]) / D;
+          if (a.noise)
+            for (int c = 0; c < 3; ++c) Fh[c] = -((gam * dv[c] + C(0.5) * al * Fi[c]) - zeta[c]) / D;
+          else
+            for (int c = 0; c < 3; ++c) Fh[c] = -(gam * dv[c] + C(0.5) * al * Fi[c]) / D;
         }
       }
       const double kick = s * im;
@@ -1172,14 +1204,11 @@ static void gather_str(const PartArgs& p, const GatherArgs& a, cudaStream_t s) {
 // markers the one-lane variants keep resident at once (6 blocks of 128
 // threads per SM); below that the four-lane variant fills the GPU better
 static long long one_lane_wave() {
-  static long long w = 0;
-  if (w == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    w = (long long)(sms > 0 ? sms : 1) * 6 * GATHER_THREADS;
-  }
-  return w;
+  static long long w[MAX_DEVICES] = {0};
+  int sms = 0;
+  const int dev = device_slot(&sms);
+  if (w[dev] == 0) w[dev] = (long long)sms * 6 * GATHER_THREADS;
+  return w[dev];
 }
 
 template <typename S, bool WALLS>
@@ -1312,15 +1341,16 @@ node_moments_kernel(const PartArgs p, const GatherArgs a, const int2* __restrict
 template <typename S, bool WALLS>
 static void node_moments_sw(const PartArgs& p, const GatherArgs& a, const int2* bricks,
                             const int* count, void* mom, uint8_t* ready, cudaStream_t s) {
-  static int grid = 0;          // resident blocks on the whole GPU
-  if (grid == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static int grids[MAX_DEVICES] = {0};   // resident blocks on the whole GPU
+  int sms = 0;
+  const int dev = device_slot(&sms);
+  if (grids[dev] == 0) {
+    int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, node_moments_kernel<S, WALLS>,
                                                   MOM_THREADS, 0);
-    grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    grids[dev] = sms * (per > 0 ? per : 1);
   }
+  const int grid = grids[dev];
   const int nb = moment_brick_count(p.g);
   node_moments_kernel<S, WALLS><<<(unsigned)(nb < grid ? nb : grid), MOM_THREADS, 0, s>>>(
       p, a, bricks, count, mom, ready);
@@ -1441,6 +1471,7 @@ struct SpreadHit {
 };
 
 constexpr int SPREAD_THREADS = 256;
+constexpr int SPREAD_ROUNDS = 4;     // candidate rounds of 32 whose loads are in flight together
 
 // Spreading, one warp per live tile (a tile some stencil reaches), taken from
 // the list the gather built.  Lane l owns the cells (l & 3, (l >> 2) & 3,
@@ -1456,9 +1487,11 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
   constexpr int SN = nodes_1d<ST>();
   constexpr int WARPS = SPREAD_THREADS / 32;
   __shared__ SpreadHit<C> shit[WARPS][32];
+  __shared__ int shk[WARPS][32 * SPREAD_ROUNDS];   // hits of a candidate group, in order
   const Geom& g = p.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   SpreadHit<C>* stage = shit[wid];
+  int* hk = shk[wid];
   const StencilRecT<C>* recs = static_cast<const StencilRecT<C>*>(a.rec);
   C* F = static_cast<C*>(a.F);
   const int ntiles = g.ntx * g.nty * g.ntz;
@@ -1550,10 +1583,21 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
     }
     const int ncand = nt[0] * nt[1] * nt[2];
     // candidate markers: the ranges of the neighbour tiles, flattened; 32
-    // neighbour tiles per chunk, 32 markers per round
+    // neighbour tiles per chunk (one load each), then the candidates in
+    // groups of SPREAD_ROUNDS x 32: their reach loads are all issued before
+    // any is tested, the hits of the group are listed in candidate order in
+    // shared memory, and their stencil records are loaded 32 at a time with
+    // one load per lane.  The hits are added in candidate order (markers
+    // sorted by tile, neighbour tiles in a fixed order), so the sums do not
+    // depend on scheduling.
     for (int qbase = 0; qbase < ncand; qbase += 32) {
       const int q = qbase + lane;
-      const int qx = q % nt[0], qy = (q / nt[0]) % nt[1], qz = (q / (nt[0] * nt[1])) & (MAXNT - 1);
+      int qx, qy, qz;
+      if (nt[0] == 3 && nt[1] == 3) {    // the usual 3 x 3 x 3 neighbourhood
+        qx = q % 3; qy = (q / 3) % 3; qz = (q / 9) & (MAXNT - 1);
+      } else {
+        qx = q % nt[0]; qy = (q / nt[0]) % nt[1]; qz = (q / (nt[0] * nt[1])) & (MAXNT - 1);
+      }
       const int tx = __shfl_sync(0xffffffffu, rowv[0], qx);
       const int ty = __shfl_sync(0xffffffffu, rowv[1], qy);
       const int tz = __shfl_sync(0xffffffffu, rowv[2], qz);
@@ -1569,62 +1613,84 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
         if (lane >= off) incl += v;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
-      for (int cbase = 0; cbase < total; cbase += 32) {
-        const int cidx = cbase + lane;
-        // owning chunk lane: the first lane whose inclusive prefix exceeds cidx
-        int pos = 0;
-        for (int step = 16; step > 0; step >>= 1) {
-          const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
-          if (v <= cidx) pos += step;
+      for (int cbase = 0; cbase < total; cbase += 32 * SPREAD_ROUNDS) {
+        int kk[SPREAD_ROUNDS];
+        short4 rr[SPREAD_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < SPREAD_ROUNDS; ++r) {
+          kk[r] = -1;
+          rr[r] = make_short4(0, 0, 0, 0);
+          if (cbase + 32 * r >= total) continue;     // warp-uniform: no candidates left
+          const int cidx = cbase + 32 * r + lane;
+          // owning chunk lane: the first lane whose inclusive prefix exceeds cidx
+          int pos = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, pos + step - 1);
+            if (v <= cidx) pos += step;
+          }
+          const int ex = __shfl_sync(0xffffffffu, incl - cnt, pos);
+          const int kq = __shfl_sync(0xffffffffu, kb, pos);
+          kk[r] = cidx < total ? kq + (cidx - ex) : -1;
+          if (kk[r] >= 0) rr[r] = a.reach[kk[r]];
         }
-        const int ex = __shfl_sync(0xffffffffu, incl - cnt, pos);
-        const int kq = __shfl_sync(0xffffffffu, kb, pos);
-        const int kk = kq + (cidx - ex);
-        bool hit = false;
-        int e[3] = {0, 0, 0};
-        if (cidx < total) {
-          const short4 r = a.reach[kk];
-          e[0] = tile_offset(r.x, lo[0], g.nx, true);
-          e[1] = tile_offset(r.y, lo[1], g.ny, true);
-          e[2] = tile_offset(r.z, lo[2], g.nz, perz);
-          hit = (shx ? e[0] <= hi[0] - lo[0] && e[0] + SN - 1 >= 0
-                     : axis_reach<SN>(r.x, g.nx, true, lo[0], hi[0])) &&
-                (shy ? e[1] <= hi[1] - lo[1] && e[1] + SN - 1 >= 0
-                     : axis_reach<SN>(r.y, g.ny, true, lo[1], hi[1])) &&
-                (shz ? e[2] <= hi[2] - lo[2] && e[2] + SN - 1 >= 0
-                     : axis_reach<SN>(r.z, g.nz, perz, lo[2], hi[2]));
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          const StencilRecT<C>& r = recs[kk];
-          SpreadHit<C>& h = stage[lane];
-          C rw[4];
+        int nhit = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) rw[q] = r.wx[q];
-          if (shx) tile_weights_shift<SN, C>(e[0], rw, h.w[0]);
-          else tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) rw[q] = r.wy[q];
-          if (shy) tile_weights_shift<SN, C>(e[1], rw, h.w[1]);
-          else tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) rw[q] = r.wz[q];
-          if (shz) tile_weights_shift<SN, C>(e[2], rw, h.w[2]);
-          else tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
-          h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
+        for (int r = 0; r < SPREAD_ROUNDS; ++r) {
+          if (cbase + 32 * r >= total) break;       // warp-uniform
+          bool hit = false;
+          if (kk[r] >= 0) {
+            const short4 rv = rr[r];
+            const int e0 = tile_offset(rv.x, lo[0], g.nx, true);
+            const int e1 = tile_offset(rv.y, lo[1], g.ny, true);
+            const int e2 = tile_offset(rv.z, lo[2], g.nz, perz);
+            hit = (shx ? e0 <= hi[0] - lo[0] && e0 + SN - 1 >= 0
+                       : axis_reach<SN>(rv.x, g.nx, true, lo[0], hi[0])) &&
+                  (shy ? e1 <= hi[1] - lo[1] && e1 + SN - 1 >= 0
+                       : axis_reach<SN>(rv.y, g.ny, true, lo[1], hi[1])) &&
+                  (shz ? e2 <= hi[2] - lo[2] && e2 + SN - 1 >= 0
+                       : axis_reach<SN>(rv.z, g.nz, perz, lo[2], hi[2]));
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (hit) hk[nhit + __popc(m & ((1u << lane) - 1u))] = kk[r];
+          nhit += __popc(m);
         }
         __syncwarp();
-        while (mask) {
-          const int src = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const SpreadHit<C>& h = stage[src];
-          const C wxy = h.w[0][cxl] * h.w[1][cyl];
-          const C w0 = wxy * h.w[2][czl], w1 = wxy * h.w[2][czl + 2];
-          const C f0 = h.F[0], f1 = h.F[1], f2 = h.F[2];
-          acc0[0] += w0 * f0; acc0[1] += w0 * f1; acc0[2] += w0 * f2;
-          acc1[0] += w1 * f0; acc1[1] += w1 * f1; acc1[2] += w1 * f2;
+        for (int hb = 0; hb < nhit; hb += 32) {
+          const int nh = min(32, nhit - hb);
+          if (lane < nh) {
+            const StencilRecT<C>& r = recs[hk[hb + lane]];
+            SpreadHit<C>& h = stage[lane];
+            int e[3];
+            e[0] = tile_offset(r.bx, lo[0], g.nx, true);
+            e[1] = tile_offset(r.by, lo[1], g.ny, true);
+            e[2] = tile_offset(r.bz, lo[2], g.nz, perz);
+            C rw[4];
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wx[q2];
+            if (shx) tile_weights_shift<SN, C>(e[0], rw, h.w[0]);
+            else tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wy[q2];
+            if (shy) tile_weights_shift<SN, C>(e[1], rw, h.w[1]);
+            else tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wz[q2];
+            if (shz) tile_weights_shift<SN, C>(e[2], rw, h.w[2]);
+            else tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
+            h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
+          }
+          __syncwarp();
+          for (int src = 0; src < nh; ++src) {
+            const SpreadHit<C>& h = stage[src];
+            const C wxy = h.w[0][cxl] * h.w[1][cyl];
+            const C w0 = wxy * h.w[2][czl], w1 = wxy * h.w[2][czl + 2];
+            const C f0 = h.F[0], f1 = h.F[1], f2 = h.F[2];
+            acc0[0] += w0 * f0; acc0[1] += w0 * f1; acc0[2] += w0 * f2;
+            acc1[0] += w1 * f0; acc1[1] += w1 * f1; acc1[2] += w1 * f2;
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
     if (in0) store_force(F, cell0, acc0[0], acc0[1], acc0[2]);
@@ -1646,15 +1712,15 @@ spread_kernel(const PartArgs p, const SpreadArgs a) {
 template <int ST, typename C>
 static void spread_launch(const PartArgs& p, const SpreadArgs& a, cudaStream_t s) {
   // a persistent grid: as many blocks as fit on the device at once
-  static int grid = 0;
-  if (grid == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static int grids[MAX_DEVICES] = {0};
+  int sms = 0;
+  const int dev = device_slot(&sms);
+  if (grids[dev] == 0) {
+    int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spread_kernel<ST, C>, SPREAD_THREADS, 0);
-    grid = (sms > 0 ? sms : 148) * (per > 0 ? per : 1);
+    grids[dev] = sms * (per > 0 ? per : 1);
   }
-  spread_kernel<ST, C><<<grid, SPREAD_THREADS, 0, s>>>(p, a);
+  spread_kernel<ST, C><<<grids[dev], SPREAD_THREADS, 0, s>>>(p, a);
 }
 
 template <typename C>

@@ -32,6 +32,7 @@ LBC_BATCH_MAX_NX = 128
 LBC_OPT_TIMING = 2
 LBC_OPT_NODE_MOMENTS = 3
 LBC_OPT_GATHER_LANES = 4
+LBC_OPT_THERMAL_AMPLITUDE = 5
 LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,
@@ -94,9 +95,11 @@ _PROTOS = {
     "lbc_box_autotune": (_S, [_P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbc_box_invariants": (_S, [_P, _P, _P, _P]),
     "lbc_box_status": (_S, [_P]),
+    "lbc_box_check": (_S, [_P, _P]),
     "lbc_box_set_option": (_S, [_P, C.c_int32, C.c_int64]),
     "lbc_box_get_option": (_S, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "lbc_box_set_thermal": (_S, [_P, C.c_double, C.c_uint64]),
+    "lbc_box_set_stress_output": (_S, [_P, _P, C.c_size_t]),
     "lbc_box_launches_per_step": (C.c_int64, [_P]),
     "lbc_box_population_bytes": (C.c_size_t, [_P]),
     "lbc_box_lb_timing": (_S, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
@@ -224,6 +227,9 @@ class Box:
               "lbc_box_create")
         self.handle = h
         self.nparticles = 0
+        self.device = device
+        self.storage = {0: "f64", 1: "f32", 2: "f16dev", 3: "bf16dev"}[lattice.storage]
+        self._sigma = None
 
     def _s(self):
         return _stream_handle(self.stream)
@@ -315,10 +321,34 @@ class Box:
     def set_option(self, option, value):
         check(self.lib.lbc_box_set_option(self.handle, option, value), "lbc_box_set_option")
 
-    def set_thermal(self, kT, seed=0):
-        """Thermal fluctuations of the fluid at temperature kT (0: off)."""
+    def set_thermal(self, kT, seed=0, printed_amplitude=None):
+        """Thermal fluctuations at temperature kT (0: off): the fluid's
+        moments and the random force of force-coupled particles.
+        printed_amplitude: True / False selects the kick amplitude
+        (LBC_OPT_THERMAL_AMPLITUDE) first; None leaves it."""
+        if printed_amplitude is not None:
+            self.set_option(LBC_OPT_THERMAL_AMPLITUDE, 1 if printed_amplitude else 0)
         check(self.lib.lbc_box_set_thermal(self.handle, float(kT), int(seed)),
               "lbc_box_set_thermal")
+
+    def stress_output(self, enable=True):
+        """Let every LB step write the viscous stress of the populations it
+        collides into a device tensor sigma[6][nz][ny][nx] (the compute
+        type: float64 for FP64 storage, else float32), returned here; the
+        tensor is read after the step.  enable=False stops it."""
+        import torch
+        if not enable:
+            check(self.lib.lbc_box_set_stress_output(self.handle, None, 0),
+                  "lbc_box_set_stress_output")
+            self._sigma = None
+            return None
+        dt = torch.float64 if self.storage == "f64" else torch.float32
+        sig = torch.zeros((6,) + self.shape, dtype=dt, device=self.device)
+        check(self.lib.lbc_box_set_stress_output(self.handle, C.c_void_p(sig.data_ptr()),
+                                                 sig.numel() * sig.element_size()),
+              "lbc_box_set_stress_output")
+        self._sigma = sig           # kept alive while the library writes it
+        return sig
 
     def get_option(self, option):
         v = C.c_int64()
@@ -365,6 +395,11 @@ class Box:
 
     def status(self):
         return self.lib.lbc_box_status(self.handle)
+
+    def check(self):
+        """Synchronise and latch the device flags (lbc_box_check); returns
+        the box's status code (0 = ok)."""
+        return int(self.lib.lbc_box_check(self.handle, self._s()))
 
     def launches_per_step(self):
         return int(self.lib.lbc_box_launches_per_step(self.handle))

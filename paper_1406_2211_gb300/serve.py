@@ -9,6 +9,13 @@ budget is spent).  Per job the loop records admission and completion times;
 `summary` gives p50 / p99 latency (completion - arrival), jobs/s and the
 aggregate lattice-update rate.
 
+Failures are per job: a job whose box cannot be built or admitted is
+"rejected", a job whose box fails while stepping (the library latches a
+non-finite density met by an LB step, and the batch retires that member
+without stopping the others) is "failed", and `cancel` removes a job
+("cancelled"); the other jobs run on.  `summary` counts only completed jobs
+in the rates and latencies and reports the others by kind.
+
 The loop only schedules: every step runs in the library's kernels through
 the `Batch` / `Box` bindings.  `JobServer` takes a factory (create / bytes /
 result / release) and a batch object, so the host logic can be exercised
@@ -33,6 +40,7 @@ class Job:
         self.admitted = None
         self.finished = None
         self.result = None
+        self.status = None          # "ok", "failed: ...", "rejected: ...", "cancelled"
 
     @property
     def latency(self):
@@ -46,7 +54,10 @@ class JobServer:
     factory.create(job) -> box (resident, initialised)
     factory.result(box) -> whatever the caller wants kept (read after the
                            batch has finished the box)
+    factory.status(box) -> (optional) 0 if the box's run succeeded, else an
+                           error description
     factory.release(box) -> frees the box's device memory
+    batch.remove(box) -> takes a member out (for cancellation)
     batch.add(box, steps) -> bool (False: no free slot)
     batch.advance(max_steps) -> (steps done, finished boxes)
     sync() -> waits for the enqueued work
@@ -64,6 +75,12 @@ class JobServer:
         self.sleep = sleep
         self.peak_active = 0
         self.peak_bytes = 0
+        self._cancel = set()
+
+    def cancel(self, jid):
+        """Cancel job `jid`: it leaves the queue, or the batch at the next
+        chunk boundary, with status "cancelled"."""
+        self._cancel.add(jid)
 
     def run(self, jobs):
         pending = collections.deque(sorted(jobs, key=lambda j: (j.arrival, j.id)))
@@ -72,21 +89,55 @@ class JobServer:
         used = 0
         done = []
         t0 = self.clock()
+        def close(job, status):
+            job.finished = self.clock() - t0
+            job.status = status
+            done.append(job)
+
         while pending or queue or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
+            # cancellations: queued jobs leave at once, running ones here
+            if self._cancel:
+                for job in [j for j in queue if j.id in self._cancel]:
+                    queue.remove(job)
+                    close(job, "cancelled")
+                for key, (job, box, need) in list(active.items()):
+                    if job.id in self._cancel:
+                        self.batch.remove(box)
+                        self.factory.release(box)
+                        del active[key]
+                        used -= need
+                        close(job, "cancelled")
             # admit in arrival order while a slot and the memory are free
             while queue and len(active) < self.max_active:
                 job = queue[0]
-                need = self.factory.bytes(job)
+                try:
+                    need = self.factory.bytes(job)
+                except Exception as e:              # an invalid job description
+                    queue.popleft()
+                    close(job, "rejected: %s" % e)
+                    continue
                 if need > self.memory_budget:
-                    raise ValueError("job %d needs %d bytes, more than the budget" % (job.id, need))
+                    queue.popleft()
+                    close(job, "rejected: needs %d bytes, more than the budget" % need)
+                    continue
                 if used + need > self.memory_budget:
                     break
                 queue.popleft()
-                box = self.factory.create(job)
-                if not self.batch.add(box, job.steps):
+                try:
+                    box = self.factory.create(job)
+                except Exception as e:
+                    close(job, "rejected: %s" % e)
+                    continue
+                try:
+                    admitted = self.batch.add(box, job.steps)
+                except Exception as e:              # the batch refuses this box
+                    self.factory.release(box)
+                    close(job, "rejected: %s" % e)
+                    continue
+                if not admitted:
                     self.factory.release(box)
                     queue.appendleft(job)
                     break
@@ -102,10 +153,16 @@ class JobServer:
             _, finished = self.batch.advance(self.chunk_steps)
             self.sync()
             now = self.clock() - t0
+            status_of = getattr(self.factory, "status", None)
             for box in finished:
                 job, b, need = active.pop(id(box))
                 job.finished = now
-                job.result = self.factory.result(b)
+                err = status_of(b) if status_of else 0
+                if err:
+                    job.status = "failed: %s" % err
+                else:
+                    job.status = "ok"
+                    job.result = self.factory.result(b)
                 self.factory.release(b)
                 used -= need
                 done.append(job)
@@ -114,10 +171,16 @@ class JobServer:
 
 
 def summary(jobs, elapsed):
-    """p50 / p99 latency, throughput and aggregate MLUPS of completed jobs."""
+    """p50 / p99 latency, throughput and aggregate MLUPS of completed jobs
+    (status "ok", or no status: jobs of a run without failures), and the
+    number of failed, rejected and cancelled ones."""
+    kinds = collections.Counter((j.status or "ok").split(":")[0] for j in jobs)
+    jobs = [j for j in jobs if j.status in (None, "ok")]
     lat = np.array([j.latency for j in jobs], dtype=np.float64)
     updates = float(sum(j.cells * j.steps for j in jobs))
     return {"jobs": len(jobs), "elapsed_s": elapsed,
+            "failed": kinds.get("failed", 0), "rejected": kinds.get("rejected", 0),
+            "cancelled": kinds.get("cancelled", 0),
             "jobs_per_s": len(jobs) / elapsed if elapsed > 0 else None,
             "mlups": updates / elapsed / 1e6 if elapsed > 0 else None,
             "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
@@ -169,6 +232,12 @@ class BoxFactory:
         else:
             box.set_particles(s["pos"], vel=s.get("vel"), mass=float(s.get("mass", 1.0)))
         return box
+
+    def status(self, box):
+        """0 if the box ran without a device-detected failure, else the
+        library's description of it (lbc_box_check)."""
+        st = box.check()
+        return 0 if st == 0 else self.lbc.library().lbc_status_string(st).decode()
 
     def result(self, box):
         pos, vel, fh = box.get_particles()

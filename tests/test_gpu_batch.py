@@ -177,3 +177,110 @@ def test_serving_loop_results_equal_alone_runs():
         solo.close()
         fac.release(box)
     batch.close()
+
+
+# ------------------------------------------------------------ failures
+def test_nonfinite_box_is_latched_by_the_step_path():
+    """A NaN population set from the host: the next LB step meets a
+    non-finite density, lbc_box_check latches LBC_ERR_NONFINITE (without
+    lbc_box_invariants), later steps refuse, and replacing the state clears
+    it."""
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    spec = _spec("fc32")
+    box = _make(spec)
+    assert box.check() == 0
+    f = box.get_populations()
+    f[3, 5, 6, 7] = np.nan
+    box.set_populations(f)
+    box.step(2)
+    assert box.check() == lbc.LBC_ERR_NONFINITE
+    assert box.status() == lbc.LBC_ERR_NONFINITE
+    with pytest.raises(lbc.LBCError):
+        box.step(1)
+    box.set_populations(synth.random_populations(spec["shape"], seed=11, amp=1e-3))
+    assert box.check() == 0
+    box.step(1)
+    assert box.check() == 0
+    box.close()
+
+
+def test_failed_member_is_retired_while_the_others_finish():
+    """One member of a batch gets a NaN population injected from the host.
+    The batch retires it (reported as finished, status LBC_ERR_NONFINITE)
+    without stopping the others, which end with exactly the results of the
+    same boxes advanced in a batch without it."""
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    names = ["fc32", "fluid", "mrt_bf16"]
+
+    def run(inject):
+        batch = lbc.Batch(4)
+        boxes = {n: _make(_spec(n)) for n in names}
+        if inject:
+            bad = _make(_spec("fc16"))
+            f = bad.get_populations()
+            f[0, 1, 2, 3] = np.nan
+            bad.set_populations(f)
+            assert batch.add(bad, 40)
+        for n in names:
+            assert batch.add(boxes[n], BUDGET[n])
+        finished = []
+        while len(batch) > 0:
+            _, fin = batch.advance(2)
+            finished.extend(fin)
+        batch.close()
+        states = {n: _state(boxes[n]) for n in names}
+        for b in boxes.values():
+            assert b.check() == 0
+            b.close()
+        if inject:
+            assert bad in finished
+            assert bad.status() == lbc.LBC_ERR_NONFINITE
+            bad.close()
+        return states
+
+    clean, mixed = run(False), run(True)
+    for n in names:
+        assert _same(clean[n], mixed[n]), n
+
+
+def test_serving_reports_failed_and_rejected_jobs():
+    """The serving loop on the GPU: a job whose box is set up with a NaN
+    population ends as "failed" with the library's reason, a job whose box
+    the batch refuses (x-rows longer than the batched launch takes) as
+    "rejected", and the other jobs complete."""
+    require_cuda()
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    from paper_1406_2211_gb300.serve import BoxFactory, Job, JobServer, summary
+
+    class Injecting(BoxFactory):
+        def create(self, job):
+            box = super().create(job)
+            if job.spec.get("nan"):
+                f = box.get_populations()
+                f[1, 2, 3, 4] = np.nan
+                box.set_populations(f)
+            return box
+
+    rng = np.random.default_rng(3)
+    jobs = []
+    for i, (L, nan) in enumerate([(16, False), (20, True), (12, False), (130, False),
+                                  (18, False)]):
+        M = 5
+        spec = dict(edge=L, storage="f32", gamma=2.0, pos=rng.uniform(0, L, (M, 3)),
+                    vel=np.zeros((M, 3)), nan=nan)
+        jobs.append(Job(i, spec, 0.0, 30, L ** 3))
+    batch = lbc.Batch(8)
+    srv = JobServer(Injecting(), batch, 2 ** 34, 8, chunk_steps=10, sync=torch.cuda.synchronize)
+    done = srv.run(jobs)
+    batch.close()
+    by = {j.id: j for j in done}
+    assert sorted(by) == [0, 1, 2, 3, 4]
+    assert by[1].status.startswith("failed") and "non-finite" in by[1].status
+    assert by[3].status.startswith("rejected")
+    for i in (0, 2, 4):
+        assert by[i].status == "ok" and np.isfinite(by[i].result["pos"]).all()
+    s = summary(done, srv.elapsed)
+    assert (s["jobs"], s["failed"], s["rejected"]) == (3, 1, 1)

@@ -175,3 +175,110 @@ def test_kicks_conserve_mass_and_momentum():
         f = F.step_recombined_fluct(f, None, None, p, kT=1e-4, seed=9, step=s)
     assert abs(L.density(f).sum() - m0) < 1e-12
     assert np.abs(L.momentum(f).reshape(3, -1).sum(axis=1) - j0).max() < 1e-12
+
+
+# ------------------------------------------------------- particle noise zeta
+# Pins of the random force of the force coupling (Sec. 5.2,
+# Eq. [viscous-coupling], Eq. [modified-force]).  On a one-cell periodic box
+# the trilinear stencil puts a particle on one node, and the fluid's kicks
+# leave its momentum alone, so the relative velocity w = v - u follows the
+# linear recurrence of the coupling alone.  Each Crank-Nicolson half step
+# (x = (alpha + beta)/2) maps w -> (1 - x)/(1 + x) w + 2x/(gamma (1 + x)) zeta,
+# and with <zeta^2> = 2 k_B T gamma / s its stationary variance is
+#   <w_a^2> = k_B T (1/m + 1/rho),
+# the canonical value of the two-body system, for any step; the explicit
+# first-order step (y = gamma h (1/m + 1/rho)) gives k_B T (1/m + 1/rho)
+# 2/(2 - y).  A wrong amplitude, a missing factor of two, the noise applied
+# to one side only or with the wrong sign, or a noise repeated from step to
+# step fails these (the last also breaks the momentum budget below).
+
+def _one_cell_variance(order, mode, n, gamma, mass, steps, kind="fc"):
+    from oracle import coupling as OC
+    from oracle import sim as OS
+    p = OL.LBParams(collision="mrt", tau=1.0)
+    parts = OC.Particles(np.array([[0.3, 0.6, 0.2]]), vel=np.zeros((1, 3)),
+                         mass=np.array([mass]))
+    sm = OS.Sim((1, 1, 1), p, OS.CouplingParams(kind, order, "trilinear", gamma=gamma,
+                                                substeps=n, mode=mode), parts)
+    kT = 1e-4
+    sm.set_thermal(kT, 77)
+    w = []
+    for _ in range(steps):
+        sm.step()
+        w.append(sm.parts.vel[0] - sm.fluid_velocity()[:, 0, 0, 0])
+    w = np.array(w[100:])
+    return (w * w).mean() / (kT * (1.0 / mass + 1.0)), sm
+
+
+@pytest.mark.parametrize("order,mode,n,gamma,mass", [
+    (2, "base", 1, 1.0, 1.0), (2, "base", 1, 3.0, 0.5), (2, "inside", 3, 2.0, 1.0),
+    (2, "outside", 2, 1.5, 1.0), (1, "base", 1, 0.5, 1.0)])
+def test_particle_noise_one_cell_equipartition(order, mode, n, gamma, mass):
+    ratio, _ = _one_cell_variance(order, mode, n, gamma, mass, 4000)
+    if order == 1:
+        y = gamma * (1.0 / mass + 1.0)
+        ratio /= 2.0 / (2.0 - y)
+    # 4000 steps of a recurrence with memory g <= 1/9 per step: about 1.3 %
+    # standard error on three components
+    assert abs(ratio - 1.0) < 0.06, ratio
+
+
+def test_original_ebf_noise_uses_its_friction():
+    """The original EBF is force coupling with gamma = rho a^3 / h: its noise
+    has that friction's amplitude (the one-cell variance is canonical)."""
+    ratio, _ = _one_cell_variance(2, "base", 1, 0.0, 1.0, 4000, kind="ebf")
+    assert abs(ratio - 1.0) < 0.06, ratio
+
+
+@pytest.mark.parametrize("order,mode,n", [(2, "base", 1), (2, "inside", 2), (2, "outside", 2),
+                                          (1, "base", 1)])
+def test_thermal_coupled_momentum_budget(order, mode, n):
+    """Fluid kicks act on non-conserved moments, and the fluid receives
+    exactly -F^h including the particles' random force: fluid plus particle
+    momentum grows by t g N to roundoff."""
+    from oracle import coupling as OC
+    from oracle import sim as OS
+    shape = (6, 5, 7)
+    rng = np.random.default_rng(4)
+    M = 9
+    g = np.array([1e-5, -2e-5, 3e-6])
+    p = OL.LBParams(collision="mrt", tau=0.9, body_force=g)
+    parts = OC.Particles(rng.uniform(0, 5, (M, 3)), vel=0.01 * rng.standard_normal((M, 3)),
+                         mass=rng.uniform(0.5, 2.0, M))
+    sm = OS.Sim(shape, p, OS.CouplingParams("fc", order, "trilinear", gamma=1.3, substeps=n,
+                                            mode=mode), parts,
+                fbar=synth.random_populations(shape, seed=2, amp=1e-3))
+    sm.set_thermal(1e-4, 9)
+    P0 = sm.total_momentum()
+    for t in range(1, 6):
+        sm.step()
+        assert np.abs(sm.total_momentum() - P0 - t * g * np.prod(shape)).max() < 1e-13
+
+
+def test_thermal_off_is_deterministic_and_counter_keeps_running():
+    """kT = 0 gives the deterministic coupled step; switching off and on with
+    the same seed continues the counter (no kick is repeated); a new seed
+    restarts it."""
+    from oracle import coupling as OC
+    from oracle import sim as OS
+    shape = (4, 4, 4)
+    rng = np.random.default_rng(6)
+
+    def make():
+        parts = OC.Particles(rng.uniform(0, 4, (3, 3)), vel=np.zeros((3, 3)), mass=np.ones(3))
+        return OS.Sim(shape, OL.LBParams(collision="bgk", tau=0.8),
+                      OS.CouplingParams("fc", 2, "trilinear", gamma=1.0), parts)
+    a, b = make(), make()
+    b.parts.pos = a.parts.pos.copy()
+    b.set_thermal(0.0, 3)
+    a.step(); b.step()
+    assert np.array_equal(a.fbar, b.fbar) and np.array_equal(a.parts.vel, b.parts.vel)
+    b.set_thermal(1e-4, 3)
+    b.step()
+    assert b.tstep == 1
+    b.set_thermal(0.0, 3)
+    b.step()
+    b.set_thermal(1e-4, 3)
+    assert b.tstep == 1                 # continues: the next kicks are step 1's
+    b.set_thermal(1e-4, 4)
+    assert b.tstep == 0                 # a new seed restarts the sequence

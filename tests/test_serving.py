@@ -132,9 +132,65 @@ def test_continuous_batching_admits_while_others_run():
 
 
 def test_job_larger_than_budget_is_rejected():
-    jobs = [Job(0, {}, 0.0, 10, 10 ** 6)]
-    with pytest.raises(ValueError):
-        _run(jobs, budget=100)
+    jobs = [Job(0, {}, 0.0, 10, 10 ** 6), Job(1, {}, 0.0, 5, 4)]
+    srv, fac, batch, done = _run(jobs, budget=100)
+    by = {j.id: j for j in done}
+    assert by[0].status.startswith("rejected") and by[0].result is None
+    assert by[1].status == "ok" and by[1].result == 5     # the other job ran
+    s = summary(done, srv.elapsed)
+    assert s["jobs"] == 1 and s["rejected"] == 1
+
+
+class FailingFactory(FakeFactory):
+    """Job ids in `bad_spec` have a description the factory cannot build;
+    boxes of jobs in `blow_up` report a device failure when they finish (as
+    a box whose LB steps met a non-finite density does)."""
+
+    def __init__(self, bad_spec=(), blow_up=()):
+        super().__init__()
+        self.bad_spec, self.blow_up = set(bad_spec), set(blow_up)
+
+    def create(self, job):
+        if job.id in self.bad_spec:
+            raise ValueError("invalid job description")
+        return super().create(job)
+
+    def status(self, box):
+        return "non-finite density" if box["job"] in self.blow_up else 0
+
+
+class RemovableBatch(FakeBatch):
+    def remove(self, box):
+        self.members = [m for m in self.members if m[0] is not box]
+
+
+def test_failed_rejected_and_cancelled_jobs_leave_the_others_running():
+    jobs = _jobs(12, 7, rate=None)
+    clock = Clock()
+    fac = FailingFactory(bad_spec={3}, blow_up={5})
+    batch = RemovableBatch(4, clock)
+    batch.cells = {j.id: j.cells for j in jobs}
+    jobs[8].steps = 10 ** 6                     # long enough to be cancelled while running
+    srv = JobServer(fac, batch, 10 ** 9, 4, chunk_steps=7, clock=clock, sleep=clock.sleep)
+    srv.cancel(11)                              # cancelled while queued
+    orig = batch.advance
+
+    def advance(k):                             # cancel job 8 once it runs
+        if any(m[0]["job"] == 8 for m in batch.members):
+            srv.cancel(8)
+        return orig(k)
+    batch.advance = advance
+    done = srv.run(jobs)
+    by = {j.id: j for j in done}
+    assert sorted(by) == list(range(12))
+    assert by[3].status.startswith("rejected")
+    assert by[5].status == "failed: non-finite density" and by[5].result is None
+    assert by[8].status == "cancelled" and by[11].status == "cancelled"
+    for i in set(range(12)) - {3, 5, 8, 11}:
+        assert by[i].status == "ok" and by[i].result == jobs[i].steps
+    assert not fac.live                         # every box released
+    s = summary(done, srv.elapsed)
+    assert (s["jobs"], s["failed"], s["rejected"], s["cancelled"]) == (8, 1, 1, 2)
 
 
 def test_summary_statistics():

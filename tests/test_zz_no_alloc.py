@@ -2,9 +2,9 @@
 box's own invariants.
 
 This entry point exists for callers that cannot allocate device memory
-(code running during CUDA-graph capture, processes whose memory is fully
-reserved by a pool, hooks holding another owner's buffer); it keeps its
-scratch in a fixed device array.  The test calls it through the C ABI on a
+(processes whose memory is fully reserved by a pool or another framework,
+hooks holding another owner's buffer); it keeps its scratch in a fixed
+device array.  The test calls it through the C ABI on a
 device copy of the populations and compares, on two calls in a row, with
 lbc_box_invariants (the existing entry point, which uses the box's arena)
 within the FP64 tolerance used by the other parity tests.  Kept in a file of
@@ -65,3 +65,25 @@ def test_noalloc_rejects_oversized_and_null():
                                         C.c_void_p(out.data_ptr()), None) == lbc.LBC_ERR_ARG
     assert lib.lbc_fbar_moments_noalloc(None, 1, 1, 1, C.c_void_p(out.data_ptr()),
                                         None) == lbc.LBC_ERR_ARG
+
+
+def test_noalloc_deepest_array_uses_every_scratch_slot():
+    """nz = LBC_NOALLOC_MAX_PLANES (the last scratch slot written), on a
+    1 x 1 x nz column whose planes carry different sums, against the
+    existing entry point's invariants, twice in a row."""
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    lib = lbc.library()
+    nz = lbc.LBC_NOALLOC_MAX_PLANES
+    shape = (nz, 1, 1)
+    lat = lbc.lattice_desc(1, 1, nz, collision="bgk", tau=0.9, storage="f64")
+    box = lbc.Box(lat)
+    box.set_populations(synth.random_populations(shape, seed=23, amp=1e-2))
+    for nsteps in (1, 2):
+        box.step(nsteps)
+        mass, mom, st = box.invariants()
+        assert st == 0
+        got = _noalloc_moments(lib, box.get_populations(), shape)
+        assert abs(got[0] - mass) < 1e-12 * mass
+        assert np.abs(got[1:] - mom).max() < 1e-12
+    box.close()
