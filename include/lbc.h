@@ -284,7 +284,15 @@ lbc_status lbc_box_check(lbc_box* box, void* stream);
 #define LBC_OPT_TIMING 2
 #define LBC_OPT_NODE_MOMENTS 3
 #define LBC_OPT_GATHER_LANES 4
+/*  LBC_OPT_LB_PAIR  16-bit storage: 1 = the plain LB step runs two cells per
+ *                  thread with packed 32-bit loads / stores and paired FP32
+ *                  arithmetic where it applies (BGK or MRT with fully relaxed
+ *                  ghosts, nx a multiple of 64; default), 0 = one cell per
+ *                  thread.  The two agree to FP32 rounding (and a 16-bit
+ *                  spacing where that rounding crosses a stochastic rounding
+ *                  step). */
 #define LBC_OPT_THERMAL_AMPLITUDE 5
+#define LBC_OPT_LB_PAIR 6
 lbc_status lbc_box_set_option(lbc_box* box, int32_t option, int64_t value);
 
 /* Current value of an option (LBC_OPT_TIMING: the event pairs reserved). */

@@ -145,6 +145,9 @@ void launch_lb_batch(int storage, const BoxEntry* boxes, int nboxes, long long r
 }
 
 void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s) {
+  // 16-bit storage: two cells per thread where the row length allows it
+  if ((storage == ST_F16 || storage == ST_BF16) && !a.pair_off && launch_lb_pair(storage, fin, fout, a, s))
+    return;
   switch (storage) {
     case ST_F64: lb_dispatch<double>(fin, fout, a, s); break;
     case ST_F32: lb_dispatch<float>(fin, fout, a, s); break;

@@ -1483,6 +1483,12 @@ lbc_status lbc_box_set_option(lbc_box* b, int32_t option, int64_t value) {
     b->gather_lanes = (int)value;
     return LBC_OK;
   }
+  if (option == LBC_OPT_LB_PAIR) {
+    if (value != 0 && value != 1) return LBC_ERR_ARG;
+    reset_graphs(b);
+    b->lb.pair_off = value ? 0 : 1;
+    return LBC_OK;
+  }
   if (option == LBC_OPT_THERMAL_AMPLITUDE) {
     if (value != 0 && value != 1) return LBC_ERR_ARG;
     reset_graphs(b);
@@ -1500,6 +1506,7 @@ lbc_status lbc_box_get_option(const lbc_box* b, int32_t option, int64_t* value) 
   else if (option == LBC_OPT_NODE_MOMENTS) *value = b->mom_on ? 1 : 0;
   else if (option == LBC_OPT_GATHER_LANES) *value = b->gather_lanes;
   else if (option == LBC_OPT_THERMAL_AMPLITUDE) *value = b->printed_amp;
+  else if (option == LBC_OPT_LB_PAIR) *value = b->lb.pair_off ? 0 : 1;
   else return LBC_ERR_ARG;
   return LBC_OK;
 }

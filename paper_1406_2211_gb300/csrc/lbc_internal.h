@@ -29,6 +29,7 @@ struct LBArgs {
   const void* Fa; const uint8_t* flag_a;
   const void* Fb; const uint8_t* flag_b;
   int block_x, block_y;   // LB launch shape (0: default rows of up to 256 cells)
+  int pair_off;           // 1: 16-bit storage uses the one-cell kernel (LBC_OPT_LB_PAIR = 0)
   float scale16;          // 16-bit storage: stored value = dev / (w_i scale16)
   float rscale16;         // 1 / scale16
   // Thermal fluctuations (Eq. [mrt-fluct]), thermal != 0: the
@@ -58,6 +59,11 @@ void launch_lb_step(int storage, const void* fin, void* fout, const LBArgs& a,
 // stress epilogue (lb_stress.cu; a.sigma must be set); both return false,
 // launching nothing, for arrays of 2^31 or more elements (32-bit indices)
 bool launch_lb_thermal(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s);
+// the plain step for 16-bit storage with two cells per thread (lb_pair.cu):
+// returns false, launching nothing, unless the storage is 16-bit, the
+// collision is BGK or MRT with fully relaxed ghosts, nx is a multiple of 64
+// and the arrays have fewer than 2^31 elements
+bool launch_lb_pair(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s);
 bool launch_lb_stress(int storage, const void* fin, void* fout, const LBArgs& a, cudaStream_t s);
 
 // One entry of a batched LB launch: a box's arguments, its source and

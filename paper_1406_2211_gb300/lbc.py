@@ -33,6 +33,7 @@ LBC_OPT_TIMING = 2
 LBC_OPT_NODE_MOMENTS = 3
 LBC_OPT_GATHER_LANES = 4
 LBC_OPT_THERMAL_AMPLITUDE = 5
+LBC_OPT_LB_PAIR = 6
 LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,

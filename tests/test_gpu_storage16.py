@@ -129,3 +129,65 @@ def test_16bit_runs_are_reproducible(storage):
     assert np.array_equal(out[0][0], out[1][0])
     for a, b in zip(out[0][1], out[1][1]):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------------ two cells per thread
+# Boxes whose rows are a multiple of 64 cells take the two-cells-per-thread
+# kernel (packed loads and stores, paired FP32 arithmetic).  Its collision is
+# the same IEEE single-precision arithmetic as the one-cell kernel with the
+# multiply-adds written out, so the two agree to FP32 rounding; each stored
+# value is then rounded stochastically with the same random bits, so they
+# differ at most by one 16-bit spacing, where the FP32 difference crosses a
+# rounding step.  Against the oracle, one step is within one 16-bit spacing
+# plus the FP32 bound.
+SPACING = {"f16dev": 2.0 ** -10, "bf16dev": 2.0 ** -7}
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+@pytest.mark.parametrize("coll,lam,walls,forced", [
+    ("bgk", (0, 0, 0, 0), False, True),
+    ("bgk", (0, 0, 0, 0), True, False),
+    ("mrt", (0, 1.3, 0, 0), False, False),        # ghosts fully relaxed
+    ("mrt", (0, 0, 0, 0), True, True),
+])
+def test_pair_kernel_matches_one_cell_kernel_and_oracle(storage, coll, lam, walls, forced):
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    from oracle import lb as OL
+    shape = (10, 12, 128)                     # nx = 128: two warps of 64 cells per row
+    nz, ny, nx = shape
+    rng = np.random.default_rng(31)
+    Fa = 1e-4 * rng.standard_normal((3,) + shape) if forced else None
+    uw = ((0.02, 0, 0), (-0.01, 0.01, 0)) if walls else ((0, 0, 0), (0, 0, 0))
+    outs = {}
+    for pair in (1, 0):
+        lat = lbc.lattice_desc(nx, ny, nz, collision=coll, tau=0.85, mrt_lambda=lam,
+                               body_force=(1e-5, 0, -2e-6), walls=walls, wall_velocity=uw,
+                               storage=storage)
+        box = lbc.Box(lat, lbc.coupling_desc("fc", 2, "trilinear"), max_particles=1)
+        box.set_option(lbc.LBC_OPT_LB_PAIR, pair)
+        assert box.get_option(lbc.LBC_OPT_LB_PAIR) == pair
+        box.set_populations(synth.random_populations(shape, seed=32, amp=1e-3))
+        f0 = box.get_populations()
+        if forced:
+            box.set_pending_force(Fa)
+        box.step(1)
+        outs[pair] = (f0, box.get_populations())
+        box.close()
+    f0, got = outs[1]
+    assert np.array_equal(f0, outs[0][0])
+    w0 = OLat.W.reshape(19, 1, 1, 1)
+    # FP32 rounding of the two forms (contractions differ) moves a value by a
+    # few 1e-9; FP16's spacing of a small deviation can be finer than that
+    sp = SPACING[storage] * np.abs(outs[0][1] - w0)
+    assert (np.abs(got - outs[0][1]) <= sp + 1e-7).all()
+    p = OL.LBParams(collision=coll, tau=0.85, mrt_lambda=lam, body_force=(1e-5, 0, -2e-6),
+                    walls=walls, u_bot=uw[0], u_top=uw[1])
+    ref = OL.step_recombined(f0, Fa, None, p)
+    if walls:
+        # reading the state back rounds the bounced-back values of the wall
+        # layers to 16 bits (the kernel uses them unrounded), and the step
+        # streams them one layer inward: compare the layers beyond
+        ref, got = ref[:, 2:-2], got[:, 2:-2]
+    bound = 1e-7 + SPACING[storage] * np.abs(ref - w0)
+    assert (np.abs(got - ref) <= bound).all(), float((np.abs(got - ref) / bound).max())
