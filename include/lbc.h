@@ -81,7 +81,8 @@ typedef int32_t lbc_status;
 #define LBC_SPLIT_OUTSIDE 2 /* F_h^1/2 [P F_int P]^n LB [P F_int P]^n F_h^1/2, Sec. 6 */
 
 typedef struct lbc_lattice_desc {
-  int32_t nx, ny, nz;        /* cells; periodic in x and y; z periodic or walls */
+  int32_t nx, ny, nz;        /* cells (1 .. 2^18 per axis, at most 2^31 in
+                                all); periodic in x and y; z periodic or walls */
   int32_t collision;         /* LBC_BGK or LBC_MRT */
   double tau;                /* lattice relaxation time: shear rate 1/tau,
                                 nu = (tau - 1/2)/3 */

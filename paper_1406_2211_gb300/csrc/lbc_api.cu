@@ -35,6 +35,9 @@ size_t elem_size(int storage) {
 bool valid_lattice(const lbc_lattice_desc* l) {
   if (!l) return false;
   if (l->nx < 1 || l->ny < 1 || l->nz < 1) return false;
+  // at most 2^18 cells per axis (the interpolation takes stencil bases from
+  // the FP64 pattern of X + 1.5 2^20, exact for |X| < 2^18)
+  if (l->nx > (1 << 18) || l->ny > (1 << 18) || l->nz > (1 << 18)) return false;
   if ((long long)l->nx * l->ny * l->nz > (1LL << 31)) return false;
   if (l->collision != LBC_BGK && l->collision != LBC_MRT) return false;
   if (!(l->tau > 0.5) && l->collision == LBC_BGK) return false;
@@ -656,9 +659,16 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     P.drift(0.5 * h, 0.0, 0.0, false, false);
   } else if (split == LBC_SPLIT_INSIDE) {
     // Eq. [multistep]: n Verlet sub-steps with coupling on each side of LB.
-    // Markers are binned once, at the first sub-step; the trailing half
-    // drift of a sub-step and the leading half drift of the next one run in
-    // one kernel (the same two FP64 updates in the same order).
+    // Every sub-step is one kernel: the drift to its force point, the
+    // intrinsic forces, the interpolation and the coupling.  Each sub-step
+    // ends with the trailing half drift of its marker and the leading half
+    // drift of the next sub-step (the same two FP64 updates in the same
+    // order), so the next one finds its marker and the bond partners at
+    // their force points; the last one ends with the trailing half drift
+    // alone and writes the binning keys of these end-of-step positions,
+    // with the flag that makes the next step re-sort (markers move far less
+    // than the half cell the bins tolerate).  Only the first step after new
+    // particles computes keys in a kernel of its own.
     const int n = b->cpl.substeps;
     const double dt = 0.5 * h / n;
     for (int half = 0; half < 2; ++half) {
@@ -667,18 +677,39 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
         // the drift of a sub-step runs inside its gather, except the
         // first one, whose keys the sort needs first
         DriftArgs fd{};
-        const bool fused = !(half == 0 && k == 0) && P.on();
-        if (half == 0 && k == 0) {
-          P.drift(0.5 * dt, 0.0, 0.0, true, true);
+        const bool first = half == 0 && k == 0, last = half == 1 && k == n - 1;
+        const bool fused = P.on();
+        if (first && fused) {
+          if (!b->binned) P.drift(0.0, 0.0, 0.0, false, true, false);   // keys of the positions
           P.sort();
-        } else if (fused) {
-          fd = P.drift_setup(0.5 * dt, 0.0, 0.0, true, false, true, nullptr, 0.5 * dt);
+        }
+        if (fused) {
+          // the first sub-step drifts its marker and the bond partners by
+          // half a sub-step from the end-of-step positions; the others find
+          // them at their force points
+          fd = P.drift_setup(first ? 0.5 * dt : 0.0, 0.0, 0.0, true, false, true);
+          fd.at_force_point = first ? 0 : 1;
+          fd.pos_out = nullptr;             // the gather writes the next force point
         }
         GatherArgs a = P.gather_base();
         if (fused) {
           a.fused = 1;
           a.drift = fd;
         }
+        int* next_flags = b->iptr(b->L.off_sortflags) + 2 * (1 - P.par);
+        if (first) a.clear_next = next_flags;
+        if (last) {
+          a.key_out = b->uptr(b->L.off_key[1]);
+          a.idx_out = b->uptr(b->L.off_idx[1]);
+          a.home = b->uptr(b->L.off_home);
+          a.need_next = next_flags;
+        }
+        // position of the next force evaluation, written after the kick
+        // into the buffer the drift's outputs go to (no thread reads it in
+        // this kernel)
+        a.pos_next = a.pos;
+        a.post_a = 0.5 * dt;
+        a.post_b = (half == 1 && k == n - 1) ? 0.0 : 0.5 * dt;
         a.mode = GM_COUPLE; a.s = make_real(dt); a.include_int = 1; a.rec_weight = make_real(1.0 / n);
         // node moments are cached at the first sub-step after the LB step
         // and reused until the next one (the first half of the next step
@@ -698,7 +729,6 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
       }
       if (half == 0) P.lb(b->F(ia), b->F(ib), 0.5 * h, 0.5 * h, h);
     }
-    P.drift(0.5 * dt, 0.0, 0.0, false, false);
   } else {
     // Sec. 6 split with the coupling outside: F_h^1/2 [P F_int P]^n LB
     // [P F_int P]^n F_h^1/2

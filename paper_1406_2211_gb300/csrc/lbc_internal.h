@@ -154,6 +154,10 @@ struct RigidArgs {
 //   v <- v + dt_kick F / m; r <- wrap(r + dt_post v)
 struct DriftArgs {
   double dt_pre0, dt_pre, dt_kick, dt_post;
+  // the stored positions are already those at which forces are evaluated
+  // (written by the previous coupling sub-step): no pre-drift of the
+  // marker or its bond partners (dt_pre0, dt_pre unused)
+  int at_force_point;
   int compute_force;     // evaluate F_int at the pre-drifted positions
   int write_key;         // tile key of the final positions
   const double* pos_in; const double* vel_in;   // [3][M]
@@ -240,6 +244,20 @@ struct GatherArgs {
   // its marker (mode GM_COUPLE; positions, velocities and F_int come from it)
   int fused;
   DriftArgs drift;
+  // GM_COUPLE: after the kick, pos_next (if set) receives the position of
+  // the next force evaluation, wrap((X + post_a v) + post_b v) (the
+  // trailing drift of this sub-step and the leading one of the next)
+  double* pos_next;
+  double post_a, post_b;
+  // binning for the next step, written from the pos_next positions when
+  // key_out is set: tile key and index of every marker, and need_next
+  // raised if a marker is more than half a cell outside its home tile
+  // (home); clear_next (if set) is the next step's flag pair, zeroed by
+  // slot 0 (the step's first sub-step, before the last one raises it)
+  uint32_t* key_out; uint32_t* idx_out;
+  const uint32_t* home;
+  int* need_next;
+  int* clear_next;
   // particles
   const uint32_t* perm;           // sorted order (null: identity)
   const uint32_t* keys;           // sorted home tile of each slot (null: no check)

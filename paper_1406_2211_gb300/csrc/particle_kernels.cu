@@ -94,6 +94,40 @@ __device__ inline void stencil_1d(double X, int& b, C (&w)[4]) {
 
 template <int ST> __host__ __device__ constexpr int nodes_1d() { return ST == 0 ? 2 : (ST == 1 ? 4 : 3); }
 
+// The same stencil with FP32 weights from one FP64 operation: for
+// |X| < 2^18, y = X + 1.5 2^20 (+ 1/2 for the three-point stencil's
+// rounding) has an ulp of 2^-32, so bits 32..51 of its pattern hold
+// floor(X) + 2^19 and bits 0..31 the fraction in units of 2^-32 (rounded to
+// nearest; a fraction that rounds up to 1 carries into the integer part
+// with fraction 0, which gives the same weights on the same nodes).  The
+// fraction's top 23 bits make the FP32 t in [0, 1).  Replaces floor,
+// conversion, subtraction and narrowing in FP64 (a small fraction of the
+// FP32 rate on this GPU) by integer operations.
+template <int ST>
+__device__ inline void stencil_1d_f32(double X, int& b, float (&w)[4]) {
+  const double y = X + (ST == 2 ? 1572864.5 : 1572864.0);
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(y));
+  const int fl = (int)((uint32_t)(u >> 32) & 0xFFFFFu) - (1 << 19);
+  const float t = __uint_as_float(0x3F800000u | ((uint32_t)u >> 9)) - 1.0f;
+  if (ST == 0) {
+    b = fl;
+    w[0] = 1.0f - t; w[1] = t; w[2] = 0.0f; w[3] = 0.0f;
+  } else if (ST == 1) {
+    b = fl - 1;
+    w[0] = phi4_outer<float>(1.0f + t);
+    w[1] = phi4_inner<float>(t);
+    w[2] = phi4_inner<float>(1.0f - t);
+    w[3] = phi4_outer<float>(2.0f - t);
+  } else {                             // t - 1/2 in [-1/2, 1/2): X - round(X)
+    b = fl - 1;
+    const float r = t - 0.5f;
+    w[0] = phi3_outer<float>(1.0f + r);
+    w[1] = phi3_inner<float>(fabsf(r));
+    w[2] = phi3_outer<float>(1.0f - r);
+    w[3] = 0.0f;
+  }
+}
+
 // ------------------------------------------------------------ periodic helpers
 // X into [0, n) for X in (-n, 2n): the same result as r = fmod(X, n), + n if
 // negative, - n if that rounded up to n, without the FP64 fmod
@@ -124,6 +158,31 @@ __device__ inline uint32_t key_of(const Geom& g, double x, double y, double z) {
   return (uint32_t)tile_of(g, ix, iy, iz);
 }
 
+// Markers keep their bins while they are within half a cell of their home
+// tile: over a step they then stay within the one cell the spreading's
+// neighbour search allows (they move far less than half a cell per step);
+// otherwise the next step re-sorts.
+__device__ inline bool near_home(const Geom& g, uint32_t home, const double (&r)[3]) {
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const bool per[3] = {true, true, !g.walls};
+  const int t = (int)home;
+  const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+  bool inside = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lo = tt[c] * TILE, w = min(lo + TILE, n3[c]) - lo;
+    if (per[c] && n3[c] <= 3 * TILE) continue;      // the search covers the axis
+    double dd = r[c] - (double)lo;
+    if (per[c]) {
+      const double h = 0.5 * n3[c];
+      if (dd < -h) dd += n3[c];
+      else if (dd >= h) dd -= n3[c];
+    }
+    inside = inside && dd >= -0.5 && dd < (double)w + 0.5;
+  }
+  return inside;
+}
+
 // ------------------------------------------------------------ drift / forces
 // One marker's sub-step (see DriftArgs): writes its new position, velocity,
 // intrinsic force and key, and returns the position, velocity and force.
@@ -138,10 +197,18 @@ __device__ __forceinline__ void drift_one(const PartArgs& p, const DriftArgs& d,
   // the box); only the final position is wrapped, and bond vectors use the
   // minimum image, so no FP64 work is spent on wrapping in between
   double r1[3];
+  if (d.at_force_point) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    v[c] = d.vel_in[c * M + i];
-    r1[c] = (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
+    for (int c = 0; c < 3; ++c) {
+      v[c] = d.vel_in[c * M + i];
+      r1[c] = d.pos_in[c * M + i];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = d.vel_in[c * M + i];
+      r1[c] = (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
+    }
   }
   F[0] = F[1] = F[2] = C(0);
   if (d.compute_force) {
@@ -156,8 +223,13 @@ __device__ __forceinline__ void drift_one(const PartArgs& p, const DriftArgs& d,
       double dist2 = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double vj = d.vel_in[c * M + j];
-        const double rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
+        double rj;
+        if (d.at_force_point) {
+          rj = d.pos_in[c * M + j];
+        } else {
+          const double vj = d.vel_in[c * M + j];
+          rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
+        }
         e[c] = rj - r1[c];
         if (sizeof(C) == 4 && per[c]) {
           // minimum image: the FP32 copy decides unless it lies within
@@ -210,9 +282,14 @@ __device__ __forceinline__ void drift_one(const PartArgs& p, const DriftArgs& d,
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c] += kick * (double)F[c];
   }
+  if (d.at_force_point && d.dt_post == 0.0) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-    r2[c] = wrap_axis(d.dt_post != 0.0 ? r1[c] + d.dt_post * v[c] : r1[c], n3[c], per[c]);
+    for (int c = 0; c < 3; ++c) r2[c] = r1[c];          // stored wrapped
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      r2[c] = wrap_axis(d.dt_post != 0.0 ? r1[c] + d.dt_post * v[c] : r1[c], n3[c], per[c]);
+  }
   if (d.pos_out)
     for (int c = 0; c < 3; ++c) d.pos_out[c * M + i] = r2[c];
   if (d.vel_out)
@@ -224,28 +301,7 @@ __device__ __forceinline__ void drift_one(const PartArgs& p, const DriftArgs& d,
       d.clear_flags[0] = 0;
       d.clear_flags[1] = 0;
     }
-    if (d.home) {
-      // markers keep their bins while they are within half a cell of their
-      // home tile: over the step they then stay within the one cell the
-      // spreading's neighbour search allows (they move far less than half
-      // a cell per step); otherwise the step re-sorts
-      const int t = (int)d.home[i];
-      const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
-      bool inside = true;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int lo = tt[c] * TILE, w = min(lo + TILE, n3[c]) - lo;
-        if (per[c] && n3[c] <= 3 * TILE) continue;      // the search covers the axis
-        double dd = r2[c] - (double)lo;
-        if (per[c]) {
-          const double h = 0.5 * n3[c];
-          if (dd < -h) dd += n3[c];
-          else if (dd >= h) dd -= n3[c];
-        }
-        inside = inside && dd >= -0.5 && dd < (double)w + 0.5;
-      }
-      if (!inside) *d.need = 1;
-    }
+    if (d.home && !near_home(g, d.home[i], r2)) *d.need = 1;
   }
 }
 
@@ -965,11 +1021,18 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
     for (int c = 0; c < 3; ++c) X[c] = P[c * M + i];
   }
   const int home = a.keys ? (int)a.keys[k] : 0;
+  if (k == 0 && sub == 0 && a.clear_next) {      // the next step's flags (read by none now)
+    a.clear_next[0] = 0;
+    a.clear_next[1] = 0;
+  }
 
   int b[3];
   C w[3][4];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) stencil_1d<ST, C>(X[c], b[c], w[c]);
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (sizeof(C) == 4) stencil_1d_f32<ST>(X[c], b[c], w[c]);
+    else stencil_1d<ST, C>(X[c], b[c], w[c]);
+  }
 
   C own[3] = {C(0), C(0), C(0)};
   if (a.mode != GM_IBM1) {
@@ -1083,10 +1146,26 @@ gather_kernel(const PartArgs p, const GatherArgs a) {
         }
       }
       const double kick = s * im;
+      double vn[3];
       for (int c = 0; c < 3; ++c) {
-        a.vel[c * M + i] = v[c] + kick * (double)(Fh[c] + Fi[c]);
+        vn[c] = v[c] + kick * (double)(Fh[c] + Fi[c]);
+        a.vel[c * M + i] = vn[c];
         if (a.fh_out) static_cast<C*>(a.fh_out)[c * M + i] = Fh[c];
         Frec[c] = -rv<C>(a.rec_weight) * Fh[c];
+      }
+      // the drift to the next force evaluation (done here once, instead of
+      // by every reader of this marker's position)
+      if (a.pos_next) {
+        double rn[3];
+        for (int c = 0; c < 3; ++c) {
+          rn[c] = wrap_axis((X[c] + a.post_a * vn[c]) + a.post_b * vn[c], n3[c], per[c]);
+          a.pos_next[c * M + i] = rn[c];
+        }
+        if (a.key_out) {            // the next step's binning, from these positions
+          a.key_out[i] = key_of(g, rn[0], rn[1], rn[2]);
+          a.idx_out[i] = (uint32_t)i;
+          if (a.home && !near_home(g, a.home[i], rn)) *a.need_next = 1;
+        }
       }
       break;
     }
