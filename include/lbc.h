@@ -373,11 +373,12 @@ size_t lbc_box_population_bytes(const lbc_box* box);
 
 /* ------------------------------------------------------------ batching
  * A batch advances many independent boxes together: per time step, the
- * particle work before the LB step of every member runs concurrently (one
- * stream per member), then one batched LB launch per group of members that
- * share storage, collision kind, walls and forcing covers all their cells
- * (box table in device memory, one x-row per block), then the particle work
- * after the LB step.  Two such steps are captured once in a CUDA graph and
+ * particle work before the LB step of every member (one launch per
+ * operation for all members, or one stream per member: see
+ * LBC_BATCH_OPT_LAUNCH), then one batched LB launch per group of members
+ * that share storage, collision kind, walls and forcing covers all their
+ * cells (box table in device memory, one x-row per block), then the
+ * particle work after the LB step.  Two such steps are captured once in a CUDA graph and
  * replayed; the graph is recaptured when members join or leave.  This is
  * the continuous batching behind a serving loop: members are admitted while
  * others are in flight and leave when their step budget is spent.  The
@@ -433,6 +434,27 @@ lbc_status lbc_batch_remaining(const lbc_batch* batch, const lbc_box* box, int64
  * receives k (0 for an empty batch). */
 lbc_status lbc_batch_advance(lbc_batch* batch, int64_t max_steps, void* stream,
                              lbc_box** finished, int32_t* nfinished, int64_t* steps_done);
+
+/* How a batched step runs the members' particle work (drift, re-binning,
+ * interpolation and coupling, spreading, node moments):
+ *   LBC_BATCH_LAUNCH_BATCHED  each member's step is recorded as a list of
+ *       operations and operation t of all members with the same kernel
+ *       variant runs as one launch over a device table of their arguments
+ *       (blocks find their member by their block range); members with
+ *       rigid bodies or more than 8192 markers cannot be recorded (the
+ *       streams are used then);
+ *   LBC_BATCH_LAUNCH_STREAMS  each member's operations run on a stream of
+ *       the member's own (the launches of different members overlap);
+ *   LBC_BATCH_LAUNCH_AUTO (default)  batched while the members average at
+ *       most 1024 markers, streams otherwise.
+ * Either way a member's results are the same, bit for bit.  Setting the
+ * option drops the captured graphs.  LBC_ERR_ARG for an unknown option or
+ * value. */
+#define LBC_BATCH_OPT_LAUNCH 1
+#define LBC_BATCH_LAUNCH_AUTO 0
+#define LBC_BATCH_LAUNCH_STREAMS 1
+#define LBC_BATCH_LAUNCH_BATCHED 2
+lbc_status lbc_batch_set_option(lbc_batch* batch, int32_t option, int64_t value);
 
 /* Number of members and the kernel launches one batched step enqueues. */
 int32_t lbc_batch_size(const lbc_batch* batch);

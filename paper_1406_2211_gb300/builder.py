@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbc.so")
 
 SOURCES = ["lb_kernels.cu", "particle_kernels.cu", "lbc_api.cu", "noalloc.cu", "lb_thermal.cu",
-           "lb_stress.cu", "lb_pair.cu"]
+           "lb_stress.cu", "lb_pair.cu", "particle_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -324,14 +324,35 @@ struct Plan {
   bool after_lb = false;
   int par = 0;     // step parity (the population buffer at the start of the step)
   bool mom_after = false;   // refill the node-moment field after the LB step
+  // batch members: the particle work is recorded here (kind, arguments)
+  // instead of launched, and run with the other members' (lbc_batch_*)
+  std::vector<std::pair<int, PartEntry>>* rec = nullptr;
   bool on() const { return phase == 0 || (phase == 1) != after_lb; }
+
+  // launch (or record) one particle operation
+  void emit(int kind, const PartEntry& e) {
+    if (rec) rec->emplace_back(kind, e);
+    else launch_part_op(kind, e, s);
+  }
+  void memset(void* ptr, int value, size_t bytes) {
+    if (rec) {
+      PartEntry e{};
+      e.u.ms = MemsetArgs{ptr, value, bytes};
+      rec->emplace_back((int)OP_MEMSET, e);
+    } else {
+      cudaMemsetAsync(ptr, value, bytes, s);
+    }
+  }
 
   void moments() {
     if (!mom_after) return;
-    GatherArgs a = gather_base();
-    launch_node_moments(part_args(b), a, reinterpret_cast<const int2*>(b->arena + b->L.off_mbricks),
-                        b->iptr(b->L.off_mcount), b->arena + b->L.off_mom,
-                        reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready), s);
+    PartEntry e{};
+    e.p = part_args(b);
+    e.u.gm.g = gather_base();
+    e.u.gm.mo = MomentsArgs{reinterpret_cast<const int2*>(b->arena + b->L.off_mbricks),
+                            b->iptr(b->L.off_mcount), b->arena + b->L.off_mom,
+                            reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready)};
+    emit(OP_MOMENTS, e);
     ++n;
   }
 
@@ -390,8 +411,10 @@ struct Plan {
   void drift(double pre, double kick, double post, bool force, bool key, bool write = true,
              const double* pos_in = nullptr, double pre0 = 0.0) {
     if (!on()) return;
-    const DriftArgs d = drift_setup(pre, kick, post, force, key, write, pos_in, pre0);
-    launch_drift(part_args(b), d, s);
+    PartEntry e{};
+    e.u.d = drift_setup(pre, kick, post, force, key, write, pos_in, pre0);
+    e.p = part_args(b);
+    emit(OP_DRIFT, e);
     ++n;
   }
 
@@ -416,7 +439,7 @@ struct Plan {
       d.need = need_flag();
       d.clear_flags = b->iptr(b->L.off_sortflags) + 2 * (1 - par);
       // no bins yet: this step sorts
-      if (!b->binned) cudaMemsetAsync(d.need, 1, sizeof(int), s);
+      if (!b->binned) memset(d.need, 1, sizeof(int));
     }
     d.inv_mass = b->dptr(b->L.off_inv_mass);
     d.ext = b->arena + b->L.off_ext;
@@ -452,11 +475,16 @@ struct Plan {
     int* need = need_flag();
     int* mcount = b->mom_on ? b->iptr(b->L.off_mcount) : nullptr;
     if (b->M <= small_sort_max()) {
-      launch_small_sort_bins(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
-                             b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->L.ntiles,
-                             b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home),
-                             need, changed_flag(), mcount, s);
-      if (b->M > 0) ++n;
+      PartEntry e{};
+      e.p = part_args(b);
+      e.u.so = SortArgs{(int)b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
+                        b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->L.ntiles,
+                        b->iptr(b->L.off_tb), b->iptr(b->L.off_te), b->uptr(b->L.off_home),
+                        need, changed_flag(), mcount};
+      if (b->M > 0) {
+        emit(OP_SMALL_SORT, e);
+        ++n;
+      }
     } else {
       launch_sort(b->M, kb, b->uptr(b->L.off_key[1]), b->uptr(b->L.off_idx[1]),
                   b->uptr(b->L.off_key[0]), b->uptr(b->L.off_idx[0]), b->uptr(b->L.off_key[1]),
@@ -468,9 +496,12 @@ struct Plan {
     }
     if (mcount) {
       // the bricks the node-moment pass fills while these bins hold
-      launch_moment_bricks(b->L.g, b->iptr(b->L.off_tb), b->iptr(b->L.off_te), need,
-                           reinterpret_cast<int2*>(b->arena + b->L.off_mbricks), mcount,
-                           reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready), s);
+      PartEntry e{};
+      e.p = part_args(b);
+      e.u.br = BricksArgs{b->iptr(b->L.off_tb), b->iptr(b->L.off_te), need,
+                          reinterpret_cast<int2*>(b->arena + b->L.off_mbricks), mcount,
+                          reinterpret_cast<uint8_t*>(b->arena + b->L.off_mready)};
+      emit(OP_BRICKS, e);
       ++n;
     }
     b->binned = true;
@@ -536,7 +567,10 @@ struct Plan {
 
   void gather(const GatherArgs& a) {
     if (!on()) return;
-    launch_gather(part_args(b), a, s);
+    PartEntry e{};
+    e.p = part_args(b);
+    e.u.gm.g = a;
+    emit(OP_GATHER, e);
     ++n;
   }
 
@@ -556,15 +590,20 @@ struct Plan {
     a.live_tiles = reinterpret_cast<int4*>(b->arena + b->L.off_live);
     a.nlive = b->iptr(b->L.off_nlive);
     a.done = b->iptr(b->L.off_nlive) + 1;
-    launch_spread(part_args(b), a, s);
+    PartEntry e{};
+    e.p = part_args(b);
+    e.u.s = a;
+    emit(OP_SPREAD, e);
     ++n;
   }
 };
 
 // One time step of the configured scheme (h = 1).
-void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) {
+void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0,
+                  std::vector<std::pair<int, PartEntry>>* rec = nullptr) {
   Plan P{b, s};
   P.phase = phase;
+  P.rec = rec;
   // step parity: the population buffer at the start of the step (a phase-2
   // pass runs after its phase 1 flipped it)
   P.par = phase == 2 ? 1 - b->cur : b->cur;
@@ -576,7 +615,7 @@ void enqueue_step(lbc_box* b, cudaStream_t s, int64_t* launches, int phase = 0) 
     // force (set by lbc_box_set_pending_force) is applied once and cleared.
     if (b->L.has_particles && order2(b)) {
       P.lb(b->F(b->ia), nullptr, 0.5 * h, 0.0, h);
-      if (P.on()) cudaMemsetAsync(b->flag(b->ia), 0, b->L.ntiles, s);
+      if (P.on()) P.memset(b->flag(b->ia), 0, b->L.ntiles);
     } else {
       P.lb(nullptr, nullptr, 0.0, 0.0, h);
     }
@@ -1693,7 +1732,7 @@ struct lbc_batch {
     bool stepped;    // has taken a step in this batch (its first one eagerly)
   };
   int max_boxes;
-  BoxEntry* tables;                 // 5 regions of max_boxes entries (device)
+  char* tables;                     // kBatchRegions regions (device), see batch_region_bytes
   std::vector<Member> members;
   std::vector<cudaStream_t> streams;     // one per slot
   std::vector<cudaEvent_t> events;       // one per slot
@@ -1709,6 +1748,7 @@ struct lbc_batch {
   // memory behind health_ev and read at the next advance without waiting
   int* hhealth;
   std::vector<lbc_box*> hboxes;   // the member of each copied word
+  int launch_mode;                // LBC_BATCH_OPT_LAUNCH
   cudaEvent_t health_ev;
   bool health_pending;
 };
@@ -1716,9 +1756,116 @@ struct lbc_batch {
 namespace {
 
 constexpr int kBatchRegions = 5;   // graph[p] steps 1, 2 use regions 2p, 2p + 1; eager: 4
+// recorded particle operations per member and step that fit the batched
+// tables (more run as launches of their own)
+constexpr int kBatchOps = 40;
 
+// a region: the LB box table (max_boxes BoxEntry), then the table of the
+// batched particle operations of one step (kBatchOps x max_boxes PartEntry)
+size_t batch_part_offset(int max_boxes) {
+  return align_up((size_t)max_boxes * sizeof(BoxEntry), 256);
+}
+size_t batch_region_bytes(int max_boxes) {
+  return align_up(batch_part_offset(max_boxes) + (size_t)kBatchOps * max_boxes * sizeof(PartEntry),
+                  256);
+}
 size_t batch_table_bytes(int max_boxes) {
-  return (size_t)kBatchRegions * (size_t)max_boxes * sizeof(BoxEntry);
+  return (size_t)kBatchRegions * batch_region_bytes(max_boxes);
+}
+BoxEntry* region_boxes(const lbc_batch* B, int r) {
+  return reinterpret_cast<BoxEntry*>(B->tables + (size_t)r * batch_region_bytes(B->max_boxes));
+}
+PartEntry* region_parts(const lbc_batch* B, int r) {
+  return reinterpret_cast<PartEntry*>(B->tables + (size_t)r * batch_region_bytes(B->max_boxes) +
+                                      batch_part_offset(B->max_boxes));
+}
+
+// Whether the members' particle work is recorded and run as one launch per
+// operation for all members: possible without rigid bodies (their frame
+// kernels are launched by the plan directly) and with re-binning in one
+// block; chosen automatically while the members average at most 1024
+// markers (many small members: the per-member launches would dominate;
+// measured on 32 boxes of 32^3 with 200 markers: 0.18 against 0.44 ms per
+// batched step), per-member streams otherwise (larger members of uneven
+// sizes overlap better: 16 boxes of 37^3-119^3 with 400-3900 markers, 0.60
+// against 0.69 ms).
+bool batch_recordable(const lbc_batch* B) {
+  if (B->launch_mode == LBC_BATCH_LAUNCH_STREAMS || B->members.empty()) return false;
+  long long total = 0;
+  for (const auto& m : B->members) {
+    if (m.box->nrigid > 0 || m.box->M > small_sort_max()) return false;
+    total += m.box->M;
+  }
+  if (B->launch_mode == LBC_BATCH_LAUNCH_BATCHED) return true;
+  return total <= 1024LL * (long long)B->members.size();
+}
+
+using OpList = std::vector<std::pair<int, PartEntry>>;
+
+// Run the recorded operations of the members: operation t of every member,
+// grouped by key (kind and kernel variant), one launch per group over
+// entries appended to `host` (and copied to `dev` on `s` when `copy`; a
+// capture copies them after it ends).  Operations without a batched form,
+// and groups that no longer fit the table, run as launches of their own.
+lbc_status run_ops(lbc_batch* B, cudaStream_t s, std::vector<OpList>& ops, PartEntry* dev,
+                   std::vector<PartEntry>& host, bool copy, int64_t* launches) {
+  const size_t cap = (size_t)kBatchOps * B->max_boxes;
+  size_t T = 0;
+  for (const auto& v : ops) T = v.size() > T ? v.size() : T;
+  for (size_t t = 0; t < T; ++t) {
+    std::vector<std::pair<long long, std::vector<int>>> groups;
+    for (size_t j = 0; j < ops.size(); ++j) {
+      if (t >= ops[j].size()) continue;
+      const int kind = ops[j][t].first;
+      const PartEntry& e = ops[j][t].second;
+      const long long key = kind == OP_MEMSET ? -1 : part_op_key(kind, e);
+      if (key < 0) {
+        launch_part_op(kind, e, s);
+        if (kind != OP_MEMSET) ++*launches;
+        continue;
+      }
+      size_t gi = 0;
+      while (gi < groups.size() && groups[gi].first != key) ++gi;
+      if (gi == groups.size()) groups.emplace_back(key, std::vector<int>());
+      groups[gi].second.push_back((int)j);
+    }
+    for (const auto& grp : groups) {
+      const int kind = ops[grp.second[0]][t].first;
+      if (host.size() + grp.second.size() > cap) {
+        for (int j : grp.second) {
+          launch_part_op(kind, ops[j][t].second, s);
+          ++*launches;
+        }
+        continue;
+      }
+      const size_t first = host.size();
+      long long blocks = 0, max_m = 0, sum_m = 0;
+      for (int j : grp.second) sum_m += ops[j][t].second.p.M;
+      for (int j : grp.second) {
+        PartEntry e = ops[j][t].second;
+        e.block0 = blocks;
+        if (kind == OP_SPREAD) {
+          // the spreading runs a persistent grid over each member's live
+          // tiles: about two resident grids' worth of blocks, shared in
+          // proportion to the members' marker counts
+          const long long share = sum_m > 0 ? (spread_grid() * 2 * e.p.M + sum_m - 1) / sum_m : 1;
+          const long long own = part_op_blocks(kind, e);
+          e.nblocks = (int)(share < 1 ? 1 : (share < own ? share : own));
+        } else {
+          e.nblocks = part_op_blocks(kind, e);
+        }
+        blocks += e.nblocks;
+        if (e.p.M > max_m) max_m = e.p.M;
+        host.push_back(e);
+      }
+      if (copy)
+        CK(cudaMemcpyAsync(dev + first, host.data() + first, grp.second.size() * sizeof(PartEntry),
+                           cudaMemcpyHostToDevice, s));
+      launch_part_batch(kind, dev + first, (int)grp.second.size(), blocks, host[first], max_m, s);
+      ++*launches;
+    }
+  }
+  return LBC_OK;
 }
 
 void batch_reset_graphs(lbc_batch* B) {
@@ -1732,23 +1879,42 @@ void batch_reset_graphs(lbc_batch* B) {
   B->steady = false;
 }
 
-// Enqueue one batched step on `main`.  The box table of the LB launches is
-// built in `host` and must be on the device at `dev` before the launches
-// run: with copy = true it is copied on `main` here (eager steps); during
-// capture the caller copies it after the capture ends.
-lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vector<BoxEntry>& host,
-                      bool copy, int64_t* launches) {
+// Enqueue one batched step on `main` using table region `region`.  The box
+// table of the LB launches is built in `host` and the table of the batched
+// particle operations in `phost`; they must be on the device before the
+// launches run: with copy = true they are copied on `main` here (eager
+// steps); during capture the caller copies them after the capture ends.
+// When every member's particle work can be recorded (batch_recordable), the
+// part of each member's step before its LB step and the part after it are
+// recorded and run as one launch per operation for all members (run_ops);
+// otherwise each member's parts run on the member's own stream.
+lbc_status batch_step(lbc_batch* B, cudaStream_t main, int region, std::vector<BoxEntry>& host,
+                      std::vector<PartEntry>& phost, bool copy, int64_t* launches) {
   const int n = (int)B->members.size();
+  BoxEntry* dev = region_boxes(B, region);
+  PartEntry* pdev = region_parts(B, region);
+  const bool rec = batch_recordable(B);
+  phost.clear();
   int64_t l = 0;
-  CK(cudaEventRecord(B->fork[0], main));
-  for (int j = 0; j < n; ++j) {
-    cudaStream_t sj = B->streams[j];
-    CK(cudaStreamWaitEvent(sj, B->fork[0], 0));
-    int64_t lj = 0;
-    enqueue_step(B->members[j].box, sj, &lj, 1);
-    l += lj;
-    CK(cudaEventRecord(B->events[j], sj));
-    CK(cudaStreamWaitEvent(main, B->events[j], 0));
+  if (rec) {
+    std::vector<OpList> ops(n);
+    for (int j = 0; j < n; ++j) {
+      int64_t lj = 0;
+      enqueue_step(B->members[j].box, main, &lj, 1, &ops[j]);
+    }
+    lbc_status st = run_ops(B, main, ops, pdev, phost, copy, &l);
+    if (st != LBC_OK) return st;
+  } else {
+    CK(cudaEventRecord(B->fork[0], main));
+    for (int j = 0; j < n; ++j) {
+      cudaStream_t sj = B->streams[j];
+      CK(cudaStreamWaitEvent(sj, B->fork[0], 0));
+      int64_t lj = 0;
+      enqueue_step(B->members[j].box, sj, &lj, 1);
+      l += lj;
+      CK(cudaEventRecord(B->events[j], sj));
+      CK(cudaStreamWaitEvent(main, B->events[j], 0));
+    }
   }
   // group the recorded LB steps; rows are numbered per group in table order
   struct Key {
@@ -1796,15 +1962,25 @@ lbc_status batch_step(lbc_batch* B, cudaStream_t main, BoxEntry* dev, std::vecto
                       main);
     ++l;
   }
-  CK(cudaEventRecord(B->fork[1], main));
-  for (int j = 0; j < n; ++j) {
-    cudaStream_t sj = B->streams[j];
-    CK(cudaStreamWaitEvent(sj, B->fork[1], 0));
-    int64_t lj = 0;
-    enqueue_step(B->members[j].box, sj, &lj, 2);
-    l += lj;
-    CK(cudaEventRecord(B->events[j], sj));
-    CK(cudaStreamWaitEvent(main, B->events[j], 0));
+  if (rec) {
+    std::vector<OpList> ops(n);
+    for (int j = 0; j < n; ++j) {
+      int64_t lj = 0;
+      enqueue_step(B->members[j].box, main, &lj, 2, &ops[j]);
+    }
+    lbc_status st = run_ops(B, main, ops, pdev, phost, copy, &l);
+    if (st != LBC_OK) return st;
+  } else {
+    CK(cudaEventRecord(B->fork[1], main));
+    for (int j = 0; j < n; ++j) {
+      cudaStream_t sj = B->streams[j];
+      CK(cudaStreamWaitEvent(sj, B->fork[1], 0));
+      int64_t lj = 0;
+      enqueue_step(B->members[j].box, sj, &lj, 2);
+      l += lj;
+      CK(cudaEventRecord(B->events[j], sj));
+      CK(cudaStreamWaitEvent(main, B->events[j], 0));
+    }
   }
   B->parity ^= 1;
   *launches = l;
@@ -1831,12 +2007,11 @@ lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
   for (const auto& m : B->members)
     saved.push_back({m.box->cur, m.box->ia, m.box->pc, m.box->binned});
   std::vector<BoxEntry> host[2];
+  std::vector<PartEntry> phost[2];
   int64_t l = 0;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  BoxEntry* region0 = B->tables + (size_t)(2 * par) * B->max_boxes;
-  BoxEntry* region1 = B->tables + (size_t)(2 * par + 1) * B->max_boxes;
-  lbc_status st1 = batch_step(B, cs, region0, host[0], false, &l);
-  lbc_status st2 = batch_step(B, cs, region1, host[1], false, &l);
+  lbc_status st1 = batch_step(B, cs, 2 * par, host[0], phost[0], false, &l);
+  lbc_status st2 = batch_step(B, cs, 2 * par + 1, host[1], phost[1], false, &l);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (own) cudaStreamDestroy(cs);
@@ -1857,10 +2032,14 @@ lbc_status batch_capture(lbc_batch* B, cudaStream_t s) {
   // launches, without blocking the host (asynchronous copies from pageable
   // memory are staged before the call returns)
   CK(cudaStreamWaitEvent(s, B->done_ev, 0));
-  CK(cudaMemcpyAsync(region0, host[0].data(), host[0].size() * sizeof(BoxEntry),
-                     cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(region1, host[1].data(), host[1].size() * sizeof(BoxEntry),
-                     cudaMemcpyHostToDevice, s));
+  for (int k = 0; k < 2; ++k) {
+    if (!host[k].empty())
+      CK(cudaMemcpyAsync(region_boxes(B, 2 * par + k), host[k].data(),
+                         host[k].size() * sizeof(BoxEntry), cudaMemcpyHostToDevice, s));
+    if (!phost[k].empty())
+      CK(cudaMemcpyAsync(region_parts(B, 2 * par + k), phost[k].data(),
+                         phost[k].size() * sizeof(PartEntry), cudaMemcpyHostToDevice, s));
+  }
   cudaGraphExec_t exec;
   e = cudaGraphInstantiate(&exec, graph, 0);
   if (e != cudaSuccess) {
@@ -1915,7 +2094,7 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
   lbc_batch* B = new (std::nothrow) lbc_batch();
   if (!B) return LBC_ERR_OOM;
   B->max_boxes = max_boxes;
-  B->tables = static_cast<BoxEntry*>(arena_dev);
+  B->tables = static_cast<char*>(arena_dev);
   B->parity = 0;
   B->steady = false;
   B->launches = 0;
@@ -1929,6 +2108,7 @@ lbc_status lbc_batch_create(int32_t max_boxes, void* arena_dev, size_t arena_byt
   B->hhealth = nullptr;
   B->health_ev = nullptr;
   B->health_pending = false;
+  B->launch_mode = LBC_BATCH_LAUNCH_AUTO;
   bool ok = cudaEventCreateWithFlags(&B->fork[0], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&B->fork[1], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming) == cudaSuccess &&
@@ -2029,9 +2209,9 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
       // eager step: its table region is rewritten after the batch's earlier
       // work (the event), without the host waiting for the device
       CK(cudaStreamWaitEvent(s, B->done_ev, 0));
-      BoxEntry* region = B->tables + (size_t)4 * B->max_boxes;
       int64_t l = 0;
-      lbc_status st = batch_step(B, s, region, host, true, &l);
+      std::vector<PartEntry> phost;
+      lbc_status st = batch_step(B, s, 4, host, phost, true, &l);
       if (st != LBC_OK) return st;
       B->launches = l;
       B->steady = true;
@@ -2040,16 +2220,20 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
     }
   }
   CK(cudaEventRecord(B->done_ev, s));
-  // the members' health words, read by the next advance
-  B->hboxes.clear();
-  for (size_t j = 0; j < B->members.size(); ++j) {
-    lbc_box* b = B->members[j].box;
-    B->hboxes.push_back(b);
-    CK(cudaMemcpyAsync(B->hhealth + j, b->arena + b->L.off_health, sizeof(int),
-                       cudaMemcpyDeviceToHost, s));
+  // the members' health words, read by a later advance once the copies are
+  // done (while earlier copies are still unread, none are added: the host
+  // may run ahead of the device by many advances)
+  if (!B->health_pending) {
+    B->hboxes.clear();
+    for (size_t j = 0; j < B->members.size(); ++j) {
+      lbc_box* b = B->members[j].box;
+      B->hboxes.push_back(b);
+      CK(cudaMemcpyAsync(B->hhealth + j, b->arena + b->L.off_health, sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(B->health_ev, s));
+    B->health_pending = true;
   }
-  CK(cudaEventRecord(B->health_ev, s));
-  B->health_pending = true;
   for (auto& m : B->members) m.remaining -= k;
   for (int j = (int)B->members.size() - 1; j >= 0; --j) {
     if (B->members[j].remaining > 0) continue;
@@ -2062,6 +2246,19 @@ lbc_status lbc_batch_advance(lbc_batch* B, int64_t max_steps, void* stream, lbc_
 }
 
 int32_t lbc_batch_size(const lbc_batch* B) { return B ? (int32_t)B->members.size() : -1; }
+
+lbc_status lbc_batch_set_option(lbc_batch* B, int32_t option, int64_t value) {
+  if (!B) return LBC_ERR_ARG;
+  if (option == LBC_BATCH_OPT_LAUNCH) {
+    if (value != LBC_BATCH_LAUNCH_AUTO && value != LBC_BATCH_LAUNCH_STREAMS &&
+        value != LBC_BATCH_LAUNCH_BATCHED)
+      return LBC_ERR_ARG;
+    B->launch_mode = (int)value;
+    batch_reset_graphs(B);
+    return LBC_OK;
+  }
+  return LBC_ERR_ARG;
+}
 
 int64_t lbc_batch_launches_per_step(const lbc_batch* B) { return B ? B->launches : -1; }
 

@@ -316,6 +316,56 @@ struct SpreadArgs {
 void neighbour_tiles(const Geom& g, int maxnt, int* table);
 void launch_spread(const PartArgs& p, const SpreadArgs& a, cudaStream_t s);
 
+// ------------------------------------------------------------ batched particle work
+// One operation of a box's step, recorded instead of launched when the box
+// advances in a batch (lbc_batch_*): operation t of every member that has
+// the same key (kind and kernel variant) runs as one launch over a device
+// table of PartEntry, block ranges [block0, block0 + nblocks) per member.
+enum PartOpKind { OP_DRIFT = 1, OP_SMALL_SORT = 2, OP_GATHER = 3, OP_SPREAD = 4, OP_BRICKS = 5,
+                  OP_MOMENTS = 6, OP_MEMSET = 7 };
+struct MemsetArgs {          // a cudaMemsetAsync of the step (flags), done per box
+  void* ptr; int value; size_t bytes;
+};
+struct SortArgs {            // the single-block re-binning of launch_small_sort_bins
+  int M, key_bits;
+  const uint32_t* kin; const uint32_t* vin; uint32_t* ka; uint32_t* va;
+  int ntiles; int* tb; int* te; uint32_t* home; const int* need; int* changed; int* brick_count;
+};
+struct BricksArgs {          // launch_moment_bricks
+  const int* tb; const int* te; const int* need; int2* bricks; int* count; uint8_t* ready;
+};
+struct MomentsArgs {         // launch_node_moments (with the GatherArgs of its pulls)
+  const int2* bricks; const int* count; void* mom; uint8_t* ready;
+};
+struct alignas(16) PartEntry {
+  PartArgs p;
+  long long block0;          // first block of this box in the batched launch
+  int nblocks, pad;          // its blocks
+  union {
+    DriftArgs d;
+    struct { GatherArgs g; MomentsArgs mo; } gm;
+    SpreadArgs s;
+    SortArgs so;
+    BricksArgs br;
+    MemsetArgs ms;
+  } u;
+};
+// key of an operation (kind and the template choices of its kernel), or -1
+// if it has no batched form (it is then launched for its box alone)
+long long part_op_key(int kind, const PartEntry& e);
+// blocks one box's part of a batched launch takes
+int part_op_blocks(int kind, const PartEntry& e);
+// the spreading's resident grid on the current device (blocks)
+long long spread_grid();
+// the per-box launch of an operation (the unbatched path)
+void launch_part_op(int kind, const PartEntry& e, cudaStream_t s);
+// one launch of operation `kind` for n boxes (table in device memory, block
+// ranges in table order), total_blocks = sum of their blocks; `first` is any
+// of the entries (host copy) for the template choices; max_m the largest
+// particle count (the single-block sort's shared memory)
+void launch_part_batch(int kind, const PartEntry* table, int n, long long total_blocks,
+                       const PartEntry& first, long long max_m, cudaStream_t s);
+
 // particle momentum sum m v (FP64), one block
 void launch_particle_momentum(long long M, const double* vel, const double* mass,
                               double* out3, cudaStream_t s);

@@ -34,6 +34,8 @@ LBC_OPT_NODE_MOMENTS = 3
 LBC_OPT_GATHER_LANES = 4
 LBC_OPT_THERMAL_AMPLITUDE = 5
 LBC_OPT_LB_PAIR = 6
+LBC_BATCH_OPT_LAUNCH = 1
+LBC_BATCH_LAUNCH_AUTO, LBC_BATCH_LAUNCH_STREAMS, LBC_BATCH_LAUNCH_BATCHED = 0, 1, 2
 LBC_NOALLOC_MAX_PLANES = 4096
 
 STORAGE = {"f64": LBC_F64, "f32": LBC_F32, "f16dev": LBC_F16_DEV,
@@ -113,6 +115,7 @@ _PROTOS = {
     "lbc_batch_advance": (_S, [_P, C.c_int64, _P, C.POINTER(_P), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int64)]),
     "lbc_batch_size": (C.c_int32, [_P]),
+    "lbc_batch_set_option": (_S, [_P, C.c_int32, C.c_int64]),
     "lbc_batch_launches_per_step": (C.c_int64, [_P]),
     "lbc_batch_destroy": (_S, [_P]),
 }
@@ -477,6 +480,14 @@ class Batch:
 
     def launches_per_step(self):
         return int(self.lib.lbc_batch_launches_per_step(self.handle))
+
+    def set_launch(self, mode):
+        """How members' particle work runs: "auto", "streams" or "batched"
+        (LBC_BATCH_OPT_LAUNCH)."""
+        v = {"auto": LBC_BATCH_LAUNCH_AUTO, "streams": LBC_BATCH_LAUNCH_STREAMS,
+             "batched": LBC_BATCH_LAUNCH_BATCHED}[mode]
+        check(self.lib.lbc_batch_set_option(self.handle, LBC_BATCH_OPT_LAUNCH, v),
+              "lbc_batch_set_option")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -129,7 +129,8 @@ def test_product_package_does_not_use_the_oracle():
 def test_batch_bytes_required_host_only(lib):
     n1 = lib.lbc_batch_bytes_required(1)
     n8 = lib.lbc_batch_bytes_required(8)
-    assert n1 > 0 and n8 == 8 * n1                 # tables scale with the slots
+    # tables scale with the slots (regions are padded to 256 bytes)
+    assert n1 > 0 and 7 * n1 < n8 <= 8 * n1
     assert lib.lbc_batch_bytes_required(0) == 0
     assert lib.lbc_batch_bytes_required(2000) == 0  # above the 1024-slot limit
 

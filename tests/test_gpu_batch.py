@@ -2,8 +2,10 @@
 
 A box advanced inside a batch, next to members of other sizes, storage
 formats, coupling kinds and step budgets, must give exactly the results of
-the same box advanced alone (same kernels, same per-box arguments), and the
-same results as stepping the box on its own with lbc_box_step.
+the same box advanced alone (same kernel bodies, same per-box arguments),
+whether the members' particle work runs as one launch per operation or on
+a stream per member, and the same results as stepping the box on its own
+with lbc_box_step.
 """
 import zlib
 
@@ -77,10 +79,11 @@ NAMES = ["fc32", "fc16", "fluid", "ibm_walls", "mrt_bf16"]
 BUDGET = {"fc32": 9, "fc16": 5, "fluid": 12, "ibm_walls": 9, "mrt_bf16": 7}
 
 
-def _run_batch(names, chunk):
+def _run_batch(names, chunk, launch="auto"):
     from paper_1406_2211_gb300 import lbc
     import torch
     batch = lbc.Batch(8)
+    batch.set_launch(launch)
     boxes = {n: _make(_spec(n)) for n in names}
     for n in names:
         assert batch.add(boxes[n], BUDGET[n])
@@ -105,6 +108,17 @@ def test_member_alone_equals_member_in_mix(alone):
     mixed = _run_batch(NAMES, chunk=4)
     for n in NAMES:
         assert _same(mixed[n], alone[n]), n
+
+
+@pytest.mark.parametrize("launch", ["streams", "batched"])
+def test_both_launch_forms_give_the_same_results(alone, launch):
+    """The members' particle work as one launch per operation for all
+    members (recorded steps, device argument tables) or on a stream per
+    member: each member's results are those of the member alone, bit for
+    bit, either way."""
+    mixed = _run_batch(NAMES, chunk=4, launch=launch)
+    for n in NAMES:
+        assert _same(mixed[n], alone[n]), (n, launch)
 
 
 def test_chunking_does_not_change_results(alone):
