@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "coupled D3Q19 MLUPS & % of HBM peak; ensemble jobs/s with p50/p99 latency"
 WORKLOAD = "mrt_bead_chains_256"
 LB_KERNEL_SOURCES = ["paper_1406_2211_gb300/csrc/lb_kernels.cu",
+                     "paper_1406_2211_gb300/csrc/lb_cell.cuh",
                      "paper_1406_2211_gb300/csrc/lb_device.cuh",
                      "paper_1406_2211_gb300/csrc/lbc_common.cuh"]
 PROFILE = os.path.join(ROOT, "profiles", "lb_step_mrt_f32_256.md")
@@ -333,9 +334,10 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ other workloads
-def other_workload_boxes(name, storage):
+def other_workload_boxes(name, storage, stencil=None, kind=None, mass_scale=1.0):
     """Full-size box of the shell (IBM) or rigid-sphere (modified EBF)
-    workload with its particles set."""
+    workload with its particles set.  For the spheres: another stencil, the
+    IBM kind, or the markers' mass scaled (the immersion limit m -> 0)."""
     import numpy as np
     import synth
     from paper_1406_2211_gb300 import lbc
@@ -355,22 +357,30 @@ def other_workload_boxes(name, storage):
     else:
         pos, first, count = synth.rigid_spheres(c["nspheres"], c["radius"], c["markers"],
                                                 c["box"], seed=c["seed"])
-        mass = c["rho0"] * 4.0 / 3.0 * np.pi * c["radius"] ** 3 / c["markers"]
+        mass = mass_scale * c["rho0"] * 4.0 / 3.0 * np.pi * c["radius"] ** 3 / c["markers"]
         lat = lbc.lattice_desc(nx, ny, nz, collision=c["collision"], tau=c["tau"], storage=storage)
-        cpl = lbc.coupling_desc("mebf", 2, c["stencil"])
+        st = stencil or c["stencil"]
+        kd = kind or "mebf"
+        cpl = lbc.coupling_desc(kd, 2, st)
         box = lbc.Box(lat, cpl, max_particles=len(pos))
         box.init_equilibrium(c["rho0"], (0.0, 0.0, 0.0))
         rng = np.random.default_rng(c["seed"])
-        box.set_particles(pos, vel=0.002 * rng.standard_normal(pos.shape), mass=mass,
-                          rigid=dict(first=first, count=count, radius=c["radius"],
-                                     k=c["rigid_k"], repulsion_k=c["repulsion_k"]))
-        desc = "%d rigid spheres x %d markers (tethers k = %g), modified EBF, Peskin-4, tau = %g" % (
-            c["nspheres"], c["markers"], c["rigid_k"], c["tau"])
+        rigid = dict(first=first, count=count, radius=c["radius"], k=c["rigid_k"],
+                     repulsion_k=c["repulsion_k"])
+        if kd == "ibm":
+            box.set_particles(pos, rigid=rigid)
+        else:
+            box.set_particles(pos, vel=0.002 * rng.standard_normal(pos.shape), mass=mass,
+                              rigid=rigid)
+        desc = "%d rigid spheres x %d markers (tethers k = %g), %s, %s, tau = %g" % (
+            c["nspheres"], c["markers"], c["rigid_k"],
+            "IBM" if kd == "ibm" else "modified EBF" + (" (m x %g)" % mass_scale if mass_scale != 1.0 else ""),
+            {"peskin4": "Peskin-4", "trilinear": "trilinear", "peskin3": "3-point"}[st], c["tau"])
     return box, nx * ny * nz, desc
 
 
 OTHER_WORKLOADS = (("ibm_shells_192", ("f32", "bf16dev")),
-                   ("mebf_rigid_spheres_128", ("f32",)))
+                   ("mebf_rigid_spheres_128", ("f32", "f32_trilinear")))
 
 
 def run_other_workloads(args, peak, only=None):
@@ -386,7 +396,8 @@ def run_other_workloads(args, peak, only=None):
             continue
         out[name] = {}
         for st in storages:
-            box, cells, desc = other_workload_boxes(name, st)
+            box, cells, desc = other_workload_boxes(
+                name, st.split("_")[0], stencil="trilinear" if st.endswith("_trilinear") else None)
             shape = box.autotune()
             box.step(args.warmup)
             box.set_option(lbc.LBC_OPT_TIMING, steps + 4)
@@ -411,10 +422,57 @@ def run_other_workloads(args, peak, only=None):
             lb_avg = lb_ms / lb_n
             out[name][st] = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
                              "steps": steps, "ms_per_step": ms / steps, "lb_avg_ms": lb_avg,
-                             "lb_frac_of_peak": BYTES_PER_CELL[st] * cells / (lb_avg * 1e-3) / 1e9 / peak,
-                             "step_frac": BYTES_PER_CELL[st] * cells / (ms / steps * 1e-3) / 1e9 / peak,
+                             "lb_frac_of_peak": BYTES_PER_CELL[st.split("_")[0]] * cells / (lb_avg * 1e-3) / 1e9 / peak,
+                             "step_frac": BYTES_PER_CELL[st.split("_")[0]] * cells / (ms / steps * 1e-3) / 1e9 / peak,
                              "lb_block": list(shape), "model": desc}
+        if name.startswith("mebf_rigid"):
+            out[name]["immersion_limit"] = immersion_limit_on_gpu(args)
     return out
+
+
+def immersion_limit_on_gpu(args, steps=20, mass_scale=1e-6):
+    """Sec. 5.3, Eq. [immersion]: the modified EBF with the markers' mass
+    m -> 0 (immersion number r -> 1) becomes the immersed boundary method.
+    The full 128^3 rigid-sphere workload run both ways from the same state
+    for `steps` steps on the GPU: the largest difference of the sphere
+    centroids (expected O(m)), and each form's time per step."""
+    import numpy as np
+    import torch
+    import synth
+    c = synth.config("mebf_rigid_spheres_128")
+    L = np.array(c["box"], dtype=float)
+    res = {}
+    cents = {}
+    for label, kind, ms in (("mebf_m0", "mebf", mass_scale), ("ibm", "ibm", 1.0)):
+        box, cells, desc = other_workload_boxes("mebf_rigid_spheres_128", "f32", kind=kind,
+                                                mass_scale=ms)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        box.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pos, _, _ = box.get_particles()
+        _, _, st = box.invariants()
+        box.close()
+        torch.cuda.empty_cache()
+        if st != 0:
+            raise RuntimeError("non-finite state in the immersion-limit run (%s)" % label)
+        m = c["markers"]
+        P = pos.reshape(-1, m, 3)
+        ref = P[:, :1, :]
+        d = P - ref
+        d -= L * np.round(d / L)                  # unwrapped around the first marker
+        cents[label] = ref[:, 0, :] + d.mean(axis=1)
+        res[label + "_ms_per_step"] = e0.elapsed_time(e1) / steps
+        res[label + "_model"] = desc
+    dc = cents["mebf_m0"] - cents["ibm"]
+    dc -= L * np.round(dc / L)
+    res.update({"steps": steps, "mass_scale": mass_scale,
+                "max_centroid_difference": float(np.abs(dc).max())})
+    return res
 
 
 # ------------------------------------------------------------------ serving
@@ -463,6 +521,24 @@ def run_serving(args):
         return out
 
     n = args.serve_jobs
+    if args.serve_full:
+        # the ensemble's own job sizes (steps uniform in [1000, 20000]):
+        # capacity with every job queued at t = 0, then Poisson arrivals at
+        # 0.5, 0.8 and 1.2 of that capacity
+        n = args.serve_full
+        sat = serve(serving_jobs(n, 12345, 1))
+        sweep = {}
+        for load in (0.5, 0.8, 1.2):
+            r = serve(serving_jobs(n, 12345, 1, rate=load * sat["jobs_per_s"]))
+            sweep["%.1f" % load] = {k: r[k] for k in ("jobs_per_s", "mlups", "p50_latency_s",
+                                                     "p99_latency_s", "elapsed_s", "peak_active",
+                                                     "failed", "rejected")}
+        return {"jobs": n, "unit": "jobs/s", "capacity_jobs_per_s": sat["jobs_per_s"],
+                "capacity_mlups": sat["mlups"], "capacity_elapsed_s": sat["elapsed_s"],
+                "loads": sweep, "slots": slots, "memory_budget_bytes": budget,
+                "sample": "%d jobs of the 2000-job ensemble (same distributions, full step "
+                          "counts 1000-20000), seed 12345; capacity with all jobs queued at "
+                          "t = 0, then Poisson arrivals at 0.5 / 0.8 / 1.2 x capacity" % n}
     sat = serve(serving_jobs(n, 12345, 20))
     rate = 0.8 * sat["jobs_per_s"]
     lat = serve(serving_jobs(n, 12345, 20, rate=rate))
@@ -605,6 +681,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the ensemble serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=32)
+    # the serving measurement at the ensemble's full job sizes (N jobs, a
+    # load sweep; minutes of device time), printed as its own JSON line
+    ap.add_argument("--serve-full", type=int, default=0)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the 16-bit storage forms of the same step")
     # box edge / SCALE and particle count / SCALE^3 at the same densities: the
@@ -624,6 +703,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return 0
+    if args.serve_full:
+        if rank == 0:
+            print(json.dumps({"serving_full": run_serving(args)}))
         return 0
     if args.workload is not None:
         if rank == 0:
