@@ -35,8 +35,8 @@ size_t elem_size(int storage) {
 bool valid_lattice(const lbc_lattice_desc* l) {
   if (!l) return false;
   if (l->nx < 1 || l->ny < 1 || l->nz < 1) return false;
-  // at most 2^18 cells per axis (the interpolation takes stencil bases from
-  // the FP64 pattern of X + 1.5 2^20, exact for |X| < 2^18)
+  // at most 2^18 cells per axis (stencil bases are kept as signed 21-bit
+  // fields, and the FP32 stencils take the floor of a float copy of X)
   if (l->nx > (1 << 18) || l->ny > (1 << 18) || l->nz > (1 << 18)) return false;
   if ((long long)l->nx * l->ny * l->nz > (1LL << 31)) return false;
   if (l->collision != LBC_BGK && l->collision != LBC_MRT) return false;
@@ -68,6 +68,9 @@ struct Layout {
   size_t off_key[2], off_idx[2], off_hist, off_tb, off_te, off_rec;
   size_t off_nbr_start, off_nbr_j, off_nbr_kr, off_nbr_r0sq;
   size_t off_inv_mass, off_reach, off_ntab, off_status, off_mark, off_live, off_nlive;
+  // per-tile hit lists of the spreading (trilinear stencils)
+  bool has_hits;
+  size_t off_hcnt, off_hits;
   size_t off_home, off_sortflags;     // home tile per marker; {need, changed} per step parity
   size_t off_ncache, off_ncache_b;   // node cache of the multistep split (0 bytes if unused)
   size_t off_mom, off_mready;        // node-moment field and its ready tiles (other schemes)
@@ -130,13 +133,21 @@ Layout make_layout(const lbc_lattice_desc* l, const lbc_coupling_desc* c, int64_
     L.off_nbr_kr = take(nb2 * 2 * force_elem_bytes(l->storage));
     L.off_nbr_r0sq = take(nb2 * 8);
     L.off_inv_mass = take((size_t)M * sizeof(double));
-    L.off_reach = take((size_t)M * sizeof(short4));
+    L.off_reach = take((size_t)M * sizeof(unsigned long long));
     L.maxnt = g.ntx > g.nty ? (g.ntx > g.ntz ? g.ntx : g.ntz) : (g.nty > g.ntz ? g.nty : g.ntz);
     L.off_ntab = take((size_t)3 * L.maxnt * 8 * sizeof(int));
     L.off_status = take(sizeof(int));
     L.off_mark = take((size_t)L.ntiles * 4);
     L.off_live = take((size_t)L.ntiles * 16);
     L.off_nlive = take(2 * sizeof(int));
+    // a trilinear stencil reaches few markers per tile: the gather lists
+    // them for the spreading (a 4- or 3-point stencil's lists would mostly
+    // overflow around dense surfaces: those keep the spreading's search)
+    L.has_hits = c->stencil == LBC_TRILINEAR;
+    if (L.has_hits) {
+      L.off_hcnt = take((size_t)L.ntiles * 4);
+      L.off_hits = take((size_t)L.ntiles * SPREAD_HCAP * 4);
+    }
     L.off_home = take((size_t)M * 4);
     L.off_sortflags = take(4 * sizeof(int));
     // the coupled sub-steps of the multistep split reuse the node moments
@@ -529,12 +540,16 @@ struct Plan {
     a.inv_mass = b->dptr(b->L.off_inv_mass);
     a.fh_out = b->arena + b->L.off_fh;
     a.rec = b->arena + b->L.off_rec;
-    a.reach = reinterpret_cast<short4*>(b->arena + b->L.off_reach);
+    a.reach = reinterpret_cast<unsigned long long*>(b->arena + b->L.off_reach);
     a.keys = b->uptr(b->L.off_key[0]);
     a.status = b->iptr(b->L.off_status);
     a.mark = reinterpret_cast<uint32_t*>(b->arena + b->L.off_mark);
     a.live_tiles = reinterpret_cast<int4*>(b->arena + b->L.off_live);
     a.nlive = b->iptr(b->L.off_nlive);
+    if (b->L.has_hits) {
+      a.hcnt = reinterpret_cast<uint32_t*>(b->arena + b->L.off_hcnt);
+      a.hits = reinterpret_cast<uint32_t*>(b->arena + b->L.off_hits);
+    }
     a.ncache = b->arena + b->L.off_ncache;
     a.ncache_b = reinterpret_cast<int4*>(b->arena + b->L.off_ncache_b);
     a.lanes = b->gather_lanes;
@@ -578,7 +593,7 @@ struct Plan {
     if (!on()) return;
     SpreadArgs a{};
     a.rec = b->arena + b->L.off_rec;
-    a.reach = reinterpret_cast<const short4*>(b->arena + b->L.off_reach);
+    a.reach = reinterpret_cast<const unsigned long long*>(b->arena + b->L.off_reach);
     a.ntab = b->iptr(b->L.off_ntab);
     a.maxnt = b->L.maxnt;
     a.tile_begin = b->iptr(b->L.off_tb);
@@ -590,6 +605,10 @@ struct Plan {
     a.live_tiles = reinterpret_cast<int4*>(b->arena + b->L.off_live);
     a.nlive = b->iptr(b->L.off_nlive);
     a.done = b->iptr(b->L.off_nlive) + 1;
+    if (b->L.has_hits) {
+      a.hcnt = reinterpret_cast<uint32_t*>(b->arena + b->L.off_hcnt);
+      a.hits = reinterpret_cast<const uint32_t*>(b->arena + b->L.off_hits);
+    }
     PartEntry e{};
     e.p = part_args(b);
     e.u.s = a;
@@ -1131,6 +1150,7 @@ lbc_status lbc_box_create(const lbc_lattice_desc* lat, const lbc_coupling_desc* 
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->iptr(L.off_status), 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b->arena + L.off_mark, 0, (size_t)L.ntiles * 4) != cudaSuccess ||
+        (L.has_hits && cudaMemset(b->arena + L.off_hcnt, 0, (size_t)L.ntiles * 4) != cudaSuccess) ||
         cudaMemset(b->arena + L.off_nlive, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaMemset(b->arena + L.off_sortflags, 0, 4 * sizeof(int)) != cudaSuccess ||
         (L.has_mom && (cudaMemset(b->arena + L.off_mready, 0, (size_t)L.ntiles) != cudaSuccess ||
@@ -1357,6 +1377,7 @@ lbc_status lbc_box_set_particles(lbc_box* b, const lbc_particles_desc* p, void* 
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(b->iptr(b->L.off_status), 0, sizeof(int), s));
   CK(cudaMemsetAsync(b->arena + b->L.off_mark, 0, (size_t)b->L.ntiles * 4, s));
+  if (b->L.has_hits) CK(cudaMemsetAsync(b->arena + b->L.off_hcnt, 0, (size_t)b->L.ntiles * 4, s));
   CK(cudaMemsetAsync(b->arena + b->L.off_nlive, 0, 2 * sizeof(int), s));
   // external forces, bond constants and rest lengths in the compute type
   // (the same roundings the kernels would apply), r0^2 in FP64

@@ -266,13 +266,17 @@ struct GatherArgs {
   const double* inv_mass;
   void* fh_out;                   // [3][M] coupling force F^h, compute type
   void* rec;                      // StencilRecT<C>[M], by sorted slot
-  short4* reach;                  // stencil base per sorted slot (x, y, z)
+  unsigned long long* reach;      // stencil base per sorted slot (pack_base)
   int* status;                    // set to 1 if a marker left its home tile +- 1 cell
   // tiles a stencil reaches: mark[t] is set once per tile and the tile is
   // appended to live_tiles[0 .. *nlive) for the spreading that follows
   uint32_t* mark;
   int4* live_tiles;               // (tile, tx, ty, tz)
   int* nlive;
+  // hit lists (null: off): each marker appends its slot to the list of every
+  // tile it reaches, hits[t * SPREAD_HCAP + n] for n < SPREAD_HCAP, counting
+  // in hcnt[t] (the first to count claims the tile)
+  uint32_t* hcnt; uint32_t* hits;
   // random force zeta of the force coupling (Sec. 5.2, Eq. [modified-force])
   // when noise != 0: three standard normals from Philox4x32-10 with counter
   // (particle index, step, 8 + substep, 0) and key (tkey0, tkey1), scaled
@@ -298,9 +302,12 @@ void launch_moment_bricks(const Geom& g, const int* tb, const int* te, const int
 void launch_node_moments(const PartArgs& p, const GatherArgs& a, const int2* bricks,
                          const int* count, void* mom, uint8_t* ready, cudaStream_t s);
 
+// markers a tile's hit list holds (one per lane of the spreading warp)
+constexpr int SPREAD_HCAP = 32;
+
 struct SpreadArgs {
   const void* rec;                            // StencilRecT<C>[M]
-  const short4* reach;                        // stencil base per sorted slot
+  const unsigned long long* reach;            // stencil base per sorted slot (pack_base)
   const int* tile_begin; const int* tile_end;
   // per axis and tile, the (up to 8) tiles holding markers whose stencil can
   // reach it: ntab[(axis * maxnt + t) * 8 + q], -1 padded
@@ -310,6 +317,9 @@ struct SpreadArgs {
   uint32_t* mark;                 // marks of the gather; consumed here
   const int4* live_tiles;         // the marked tiles (t, tx, ty, tz), in any order
   int* nlive;                     // their count; reset to 0 on exit
+  // the gather's hit lists (null: off); a tile's count is reset to 0 when
+  // it is spread, and a list longer than SPREAD_HCAP takes the search
+  uint32_t* hcnt; const uint32_t* hits;
   int* done;                      // blocks finished (reset to 0 on exit)
 };
 // host: fill the neighbour-tile table (3 * maxnt * 4 ints)

@@ -63,21 +63,10 @@ __device__ inline void stencil_1d(double X, int& b, C (&w)[4]) {
 
 template <int ST> __host__ __device__ constexpr int nodes_1d() { return ST == 0 ? 2 : (ST == 1 ? 4 : 3); }
 
-// The same stencil with FP32 weights from one FP64 operation: for
-// |X| < 2^18, y = X + 1.5 2^20 (+ 1/2 for the three-point stencil's
-// rounding) has an ulp of 2^-32, so bits 32..51 of its pattern hold
-// floor(X) + 2^19 and bits 0..31 the fraction in units of 2^-32 (rounded to
-// nearest; a fraction that rounds up to 1 carries into the integer part
-// with fraction 0, which gives the same weights on the same nodes).  The
-// fraction's top 23 bits make the FP32 t in [0, 1).  Replaces floor,
-// conversion, subtraction and narrowing in FP64 (a small fraction of the
-// FP32 rate on this GPU) by integer operations.
+// FP32 weights of the stencil whose floor node is fl, for the fraction t in
+// [0, 1) (three-point stencil: fl = floor(X + 1/2), t = frac(X + 1/2))
 template <int ST>
-__device__ inline void stencil_1d_f32(double X, int& b, float (&w)[4]) {
-  const double y = X + (ST == 2 ? 1572864.5 : 1572864.0);
-  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(y));
-  const int fl = (int)((uint32_t)(u >> 32) & 0xFFFFFu) - (1 << 19);
-  const float t = __uint_as_float(0x3F800000u | ((uint32_t)u >> 9)) - 1.0f;
+__device__ inline void stencil_weights_f32(int fl, float t, int& b, float (&w)[4]) {
   if (ST == 0) {
     b = fl;
     w[0] = 1.0f - t; w[1] = t; w[2] = 0.0f; w[3] = 0.0f;
@@ -97,15 +86,84 @@ __device__ inline void stencil_1d_f32(double X, int& b, float (&w)[4]) {
   }
 }
 
+// ------------------------------------------------------------ FP64 values without FP64 work
+// The bit pattern of (double)n for 0 < n < 2^31 (integer operations).
+__device__ inline long long dbl_bits_of(int n) {
+  const int e = 31 - __clz(n);                             // n = 1.f 2^e
+  const unsigned long long f = ((unsigned long long)n << (52 - e)) & ((1ull << 52) - 1ull);
+  return (long long)(((unsigned long long)(1023 + e) << 52) | f);
+}
+
+// x as the unevaluated sum hi + lo of two floats, read off its bit pattern
+// with integer operations: hi is x cut to 24 significant bits, lo the other
+// 29 bits, rounded to 24 by the conversion, so |x - hi - lo| <= 2^-48 |x|.
+// |x| < 2^-126 (zero included) gives 0 + 0; |x| must be below 2^128.
+__device__ inline void split_df(double x, float& hi, float& lo) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  const uint32_t w1 = (uint32_t)(u >> 32), w0 = (uint32_t)u;
+  const uint32_t sign = w1 & 0x80000000u;
+  const int e = (int)((w1 >> 20) & 0x7FFu);              // biased FP64 exponent
+  if (e < 897) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | ((w1 & 0xFFFFFu) << 3) | (w0 >> 29));
+  const int le = e - 1075 + 127;                          // biased exponent of 2^(e - 1075)
+  const float scale = le >= 1 ? __uint_as_float((uint32_t)le << 23) : 0.0f;
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn(w0 & 0x1FFFFFFFu) * scale) | sign);
+}
+
+// s = fl(a + b) and the rounding error a + b - s exactly (Knuth's TwoSum)
+__device__ inline float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  err = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+  return s;
+}
+
+// A stencil base (x, y, z), each in -2^20 .. 2^20 - 1, as three signed
+// 21-bit fields of one 64-bit word (bits 0-20, 22-42, 43-63)
+__device__ inline unsigned long long pack_base(int x, int y, int z) {
+  return ((unsigned long long)(x & 0x1FFFFF)) | ((unsigned long long)(y & 0x1FFFFF) << 22) |
+         ((unsigned long long)(z & 0x1FFFFF) << 43);
+}
+__device__ inline int base_x(unsigned long long u) { return (int)((long long)(u << 43) >> 43); }
+__device__ inline int base_y(unsigned long long u) { return (int)((long long)(u << 21) >> 43); }
+__device__ inline int base_z(unsigned long long u) { return (int)((long long)u >> 43); }
+
+// The stencil of X given as hi + lo (split_df) in FP32 alone: floor of hi,
+// and the fraction (hi - floor(hi)) + lo brought into [0, 1).
+template <int ST>
+__device__ inline void stencil_1d_df(float xh, float xl, int& b, float (&w)[4]) {
+  float fl = floorf(xh);
+  float t = (xh - fl) + xl;
+  if (ST == 2) t += 0.5f;
+  if (t < 0.0f) { fl -= 1.0f; t += 1.0f; }
+  if (t >= 1.0f) { fl += 1.0f; t -= 1.0f; }
+  stencil_weights_f32<ST>((int)fl, t, b, w);
+}
+
 // ------------------------------------------------------------ periodic helpers
 // X into [0, n) for X in (-n, 2n): the same result as r = fmod(X, n), + n if
-// negative, - n if that rounded up to n, without the FP64 fmod
+// negative, - n if that rounded up to n, without the FP64 fmod.  The tests
+// are taken on the bit pattern (non-negative doubles order as their
+// patterns; -0 counts as 0), so only a coordinate that crosses the boundary
+// spends FP64 work.
 __device__ inline double wrap_axis(double X, int n, bool periodic) {
   if (!periodic) return X;
-  const double dn = (double)n;
-  if (X < 0.0) X += dn;
-  else if (X >= dn) X -= dn;
-  if (X >= dn) X -= dn;
+  const long long un = dbl_bits_of(n);
+  constexpr long long NEG_ZERO = (long long)0x8000000000000000ull;
+  long long u = __double_as_longlong(X);
+  if (u < 0 && u != NEG_ZERO) {                // X < 0
+    X += (double)n;
+    u = __double_as_longlong(X);
+  } else if (u >= un) {                        // X >= n
+    X -= (double)n;
+    u = __double_as_longlong(X);
+  }
+  if (u >= un) X -= (double)n;
   return X;
 }
 
@@ -166,6 +224,10 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
   // intermediate positions are left unwrapped (they stay within a cell of
   // the box); only the final position is wrapped, and bond vectors use the
   // minimum image, so no FP64 work is spent on wrapping in between
+  // with FP32 compute the two pre-drifts are taken as one (dt_pre0 + dt_pre)
+  // v: one FP64 rounding instead of two
+  constexpr bool F32 = sizeof(C) == 4;
+  const double dt_pre01 = F32 ? d.dt_pre0 + d.dt_pre : 0.0;
   double r1[3];
   if (d.at_force_point) {
 #pragma unroll
@@ -177,7 +239,8 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       v[c] = d.vel_in[c * M + i];
-      r1[c] = (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
+      r1[c] = F32 ? d.pos_in[c * M + i] + dt_pre01 * v[c]
+                  : (d.pos_in[c * M + i] + d.dt_pre0 * v[c]) + d.dt_pre * v[c];
     }
   }
   F[0] = F[1] = F[2] = C(0);
@@ -186,42 +249,80 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
     const C* kr = static_cast<const C*>(d.nbr_kr);
     for (int c = 0; c < 3; ++c) F[c] = ext[c * M + i];
     const int bbeg = d.nbr_start[i], bend = d.nbr_start[i + 1];
+    // FP32 compute: the marker's position as hi + lo floats (split_df)
+    float r1h[3] = {0.0f, 0.0f, 0.0f}, r1l[3] = {0.0f, 0.0f, 0.0f};
+    if (F32 && bend > bbeg)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) split_df(r1[c], r1h[c], r1l[c]);
     for (int b = bbeg; b < bend; ++b) {
       const long long j = d.nbr_j[b];
-      double e[3];
-      C ec[3];
-      double dist2 = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double rj;
-        if (d.at_force_point) {
-          rj = d.pos_in[c * M + j];
-        } else {
-          const double vj = d.vel_in[c * M + j];
-          rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
-        }
-        e[c] = rj - r1[c];
-        if (sizeof(C) == 4 && per[c]) {
-          // minimum image: the FP32 copy decides unless it lies within
-          // rounding of n/2, where the FP64 test is taken
-          float ef = (float)e[c];
-          if (fabsf(ef) >= 0.4999f * n3[c]) {
-            e[c] = min_image(e[c], n3[c], true);
-            ef = (float)e[c];
-          }
-          ec[c] = (C)ef;
-        } else {
-          e[c] = min_image(e[c], n3[c], per[c]);
-          ec[c] = (C)e[c];
-        }
-        dist2 += e[c] * e[c];
-      }
-      // stretch |d| - r0 = (|d|^2 - r0^2) / (|d| + r0): the difference of
-      // squares in FP64 (bonds sit near their rest length, where |d| - r0
-      // formed in FP32 would lose most of its digits), the rest in C
       const C k = kr[2 * b], r0 = kr[2 * b + 1];
-      const C dist = sqrt((C)dist2);
-      const C stretch = (C)(dist2 - d.nbr_r0sq[b]) / (dist + r0);
+      C ec[3];
+      C dist, D;
+      if constexpr (F32) {
+        // The bond vector e = r_j - r_i and |e|^2 - r0^2 in double-float
+        // arithmetic on the FP32 pipe: e as eh + el (TwoSum of the highs
+        // plus the difference of the lows; the minimum image subtracts n
+        // from eh exactly), |e|^2 as the exact products eh^2 (FMA residue)
+        // plus 2 eh el, summed with TwoSum against r0^2 = hi + lo.  The
+        // result matches the FP64 difference of squares to about 2^-46 |e|^2.
+        float eh[3], el[3], P[3], PE[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double rj = d.pos_in[c * M + j];
+          if (!d.at_force_point) rj += dt_pre01 * d.vel_in[c * M + j];
+          float jh, jl, err;
+          split_df(rj, jh, jl);
+          float sh = two_sum(jh, -r1h[c], err);
+          float t = err + (jl - r1l[c]);
+          float h = sh + t;                      // renormalised pair h + l
+          float l = t - (h - sh);
+          if (per[c]) {
+            const float half = 0.5f * (float)n3[c];
+            int shift = 0;
+            if (h > half || (h == half && l > 0.0f)) shift = -1;
+            else if (h < -half || (h == -half && l < 0.0f)) shift = 1;
+            if (shift != 0) {
+              const float hs = h + (float)(shift * n3[c]);   // exact (Sterbenz)
+              h = hs + l;
+              l = l - (h - hs);
+            }
+          }
+          eh[c] = h;
+          el[c] = l;
+          ec[c] = h;
+          P[c] = h * h;
+          PE[c] = fmaf(h, h, -P[c]) + 2.0f * h * l;
+        }
+        float e1, e2, e3, r0h, r0l;
+        const float S1 = two_sum(P[0], P[1], e1);
+        const float S2 = two_sum(S1, P[2], e2);
+        split_df(d.nbr_r0sq[b], r0h, r0l);
+        const float S3 = two_sum(S2, -r0h, e3);
+        D = S3 + (((e1 + e2) + e3) + ((PE[0] + PE[1]) + PE[2]) - r0l);
+        dist = sqrtf(S2);
+      } else {
+        double dist2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double rj;
+          if (d.at_force_point) {
+            rj = d.pos_in[c * M + j];
+          } else {
+            const double vj = d.vel_in[c * M + j];
+            rj = (d.pos_in[c * M + j] + d.dt_pre0 * vj) + d.dt_pre * vj;
+          }
+          const double e = min_image(rj - r1[c], n3[c], per[c]);
+          ec[c] = (C)e;
+          dist2 += e * e;
+        }
+        // the difference of squares in FP64: bonds sit near their rest
+        // length, where |d| - r0 formed directly would lose most digits
+        dist = sqrt((C)dist2);
+        D = (C)(dist2 - d.nbr_r0sq[b]);
+      }
+      // stretch |d| - r0 = (|d|^2 - r0^2) / (|d| + r0)
+      const C stretch = D / (dist + r0);
       const C mag = k * stretch / dist;
       for (int c = 0; c < 3; ++c) F[c] += ec[c] * mag;
     }
@@ -232,12 +333,19 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
       // the repulsion
       const double* fr = d.rigid.frames + 12 * body;
       const double q[3] = {d.rigid.ref[i], d.rigid.ref[M + i], d.rigid.ref[2 * M + i]};
-      const double inv_n = 1.0 / (double)d.rigid.count[body];
+      // the marker's share of the repulsion: with FP32 compute a float
+      // division (an FP64 one is a long sequence on the FP64 pipe)
+      const int cnt = d.rigid.count[body];
+      const float inv_nf = F32 ? 1.0f / (float)cnt : 0.0f;
+      const double inv_n = F32 ? 0.0 : 1.0 / (double)cnt;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double site = fr[c] + fr[3 + 3 * c] * q[0] + fr[4 + 3 * c] * q[1] + fr[5 + 3 * c] * q[2];
         const double dev = min_image(r1[c] - site, n3[c], per[c]);
-        F[c] += (C)(-d.rigid.k * dev + d.rigid.frep[3 * body + c] * inv_n);
+        if (F32)
+          F[c] += (C)(-d.rigid.k * dev) + (C)d.rigid.frep[3 * body + c] * (C)inv_nf;
+        else
+          F[c] += (C)(-d.rigid.k * dev + d.rigid.frep[3 * body + c] * inv_n);
       }
     }
     if (d.fint_out) {
@@ -772,20 +880,29 @@ __device__ inline void cache_store(double* p, const double (&j)[3], double inv) 
 template <typename C>
 __device__ __forceinline__ void node_add(const GatherArgs& a, long long cell, int tile, C wt,
                                          C (&j)[3], C inv, const C (&cgg)[3], C (&own)[3]) {
+  // each force 4-vector is loaded together with its tile's flag (it lies
+  // inside the field either way) and used only where the flag is set, so
+  // the two loads are not one after the other
   const C* F1 = static_cast<const C*>(a.F1);
-  if (F1 && a.flag1[tile]) {
+  const C* F2 = static_cast<const C*>(a.F2);
+  C f1x = C(0), f1y = C(0), f1z = C(0), f2x = C(0), f2y = C(0), f2z = C(0);
+  bool on1 = false, on2 = false;
+  if (F1) {
+    on1 = a.flag1[tile] != 0;
+    load_force(F1, cell, f1x, f1y, f1z);
+  }
+  if (F2) {
+    on2 = a.flag2[tile] != 0;
+    load_force(F2, cell, f2x, f2y, f2z);
+  }
+  if (on1) {
     const C c1 = rv<C>(a.c1);
-    C fx, fy, fz;
-    load_force(F1, cell, fx, fy, fz);
-    j[0] += c1 * fx; j[1] += c1 * fy; j[2] += c1 * fz;
+    j[0] += c1 * f1x; j[1] += c1 * f1y; j[2] += c1 * f1z;
   }
   j[0] += cgg[0]; j[1] += cgg[1]; j[2] += cgg[2];
-  const C* F2 = static_cast<const C*>(a.F2);
-  if (F2 && a.flag2[tile]) {
+  if (on2) {
     const C c2 = rv<C>(a.c2);
-    C fx, fy, fz;
-    load_force(F2, cell, fx, fy, fz);
-    j[0] += c2 * fx; j[1] += c2 * fy; j[2] += c2 * fz;
+    j[0] += c2 * f2x; j[1] += c2 * f2y; j[2] += c2 * f2z;
   }
   own[0] += wt * (j[0] * inv); own[1] += wt * (j[1] * inv); own[2] += wt * (j[2] * inv);
 }
@@ -941,8 +1058,13 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
   C w[3][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if constexpr (sizeof(C) == 4) stencil_1d_f32<ST>(X[c], b[c], w[c]);
-    else stencil_1d<ST, C>(X[c], b[c], w[c]);
+    if constexpr (sizeof(C) == 4) {
+      float xh, xl;
+      split_df(X[c], xh, xl);
+      stencil_1d_df<ST>(xh, xl, b[c], w[c]);
+    } else {
+      stencil_1d<ST, C>(X[c], b[c], w[c]);
+    }
   }
 
   C own[3] = {C(0), C(0), C(0)};
@@ -1067,9 +1189,13 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
       // the drift to the next force evaluation (done here once, instead of
       // by every reader of this marker's position)
       if (a.pos_next) {
+        // (FP32 compute: the two quarter drifts as one, (post_a + post_b) v)
+        const double post_ab = sizeof(C) == 4 ? a.post_a + a.post_b : 0.0;
         double rn[3];
         for (int c = 0; c < 3; ++c) {
-          rn[c] = wrap_axis((X[c] + a.post_a * vn[c]) + a.post_b * vn[c], n3[c], per[c]);
+          rn[c] = wrap_axis(sizeof(C) == 4 ? X[c] + post_ab * vn[c]
+                                           : (X[c] + a.post_a * vn[c]) + a.post_b * vn[c],
+                            n3[c], per[c]);
           a.pos_next[c * M + i] = rn[c];
         }
         if (a.key_out) {            // the next step's binning, from these positions
@@ -1110,7 +1236,7 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
         r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
         r.pad = C(0);
         static_cast<StencilRecT<C>*>(a.rec)[k] = r;
-        a.reach[k] = make_short4((short)b[0], (short)b[1], (short)b[2], 0);
+        a.reach[k] = pack_base(b[0], b[1], b[2]);
       }
       // claim the tiles the stencil reaches (nodes with non-zero weight); per
       // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
@@ -1137,10 +1263,23 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
 #pragma unroll
           for (int qx = 0; qx < SN; ++qx)
             if (qz % GL == sub && tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
-              uint32_t* m = a.mark + (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
-              // most tiles are claimed already: an L2 read (marks only go
-              // from 0 to 1 during the gather) spares their atomic
-              if (__ldcg(m) == 0u && atomicExch(m, 1u) == 0u) {
+              const int tile = (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
+              bool first;
+              if (a.hcnt != nullptr) {
+                // the marker joins the tile's hit list; the first to join
+                // claims the tile
+                const uint32_t slot = atomicAdd(a.hcnt + tile, 1u);
+                if (slot < (uint32_t)SPREAD_HCAP)
+                  a.hits[(size_t)tile * SPREAD_HCAP + slot] = (uint32_t)k;
+                first = slot == 0u;
+                if (first) a.mark[tile] = 1u;
+              } else {
+                // most tiles are claimed already: an L2 read (marks only go
+                // from 0 to 1 during the gather) spares their atomic
+                uint32_t* m = a.mark + tile;
+                first = __ldcg(m) == 0u && atomicExch(m, 1u) == 0u;
+              }
+              if (first) {
                 claimed |= 1ull << ((qz * SN + qy) * SN + qx);
                 ++nclaim;
               }
@@ -1464,6 +1603,69 @@ __device__ __forceinline__ void spread_body(const PartArgs& __restrict__ p,
       if (in0) load_force(F, cell0, acc0[0], acc0[1], acc0[2]);
       if (in1) load_force(F, cell1, acc1[0], acc1[1], acc1[2]);
     }
+    // adds the markers listed in hk[0 .. nhit), in that order
+    auto add_hits = [&](int nhit) {
+      for (int hb = 0; hb < nhit; hb += 32) {
+        const int nh = min(32, nhit - hb);
+        if (lane < nh) {
+          const StencilRecT<C>& r = recs[hk[hb + lane]];
+          SpreadHit<C>& h = stage[lane];
+          int e[3];
+          e[0] = tile_offset(r.bx, lo[0], g.nx, true);
+          e[1] = tile_offset(r.by, lo[1], g.ny, true);
+          e[2] = tile_offset(r.bz, lo[2], g.nz, perz);
+          C rw[4];
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wx[q2];
+          if (shx) tile_weights_shift<SN, C>(e[0], rw, h.w[0]);
+          else tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wy[q2];
+          if (shy) tile_weights_shift<SN, C>(e[1], rw, h.w[1]);
+          else tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wz[q2];
+          if (shz) tile_weights_shift<SN, C>(e[2], rw, h.w[2]);
+          else tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
+          h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
+        }
+        __syncwarp();
+        for (int src = 0; src < nh; ++src) {
+          const SpreadHit<C>& h = stage[src];
+          const C wxy = h.w[0][cxl] * h.w[1][cyl];
+          const C w0 = wxy * h.w[2][czl], w1 = wxy * h.w[2][czl + 2];
+          const C f0 = h.F[0], f1 = h.F[1], f2 = h.F[2];
+          acc0[0] += w0 * f0; acc0[1] += w0 * f1; acc0[2] += w0 * f2;
+          acc1[0] += w1 * f0; acc1[1] += w1 * f1; acc1[2] += w1 * f2;
+        }
+        __syncwarp();
+      }
+    };
+    // hit list of the tile, built by the gather (trilinear stencils): the
+    // markers whose stencil reaches it, sorted by slot so the sums run in a
+    // fixed order; a list that overflowed (or none) takes the search below
+    int hc = SPREAD_HCAP + 1;
+    if (a.hcnt != nullptr) {
+      hc = (int)a.hcnt[t];
+      uint32_t key = a.hits[(size_t)t * SPREAD_HCAP + lane];
+      if (hc <= SPREAD_HCAP) {
+        if (lane >= hc) key = 0xFFFFFFFFu;
+#pragma unroll
+        for (int kk2 = 2; kk2 <= 32; kk2 <<= 1)
+#pragma unroll
+          for (int jj = kk2 >> 1; jj > 0; jj >>= 1) {
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, key, jj);
+            const bool lower = (lane & jj) == 0, up = (lane & kk2) == 0;
+            key = lower == up ? min(key, other) : max(key, other);
+          }
+        if (lane < hc) hk[lane] = (int)key;
+        __syncwarp();
+        add_hits(hc);
+      }
+      __syncwarp();
+      if (lane == 0) a.hcnt[t] = 0u;           // empty for the next gather
+    }
+    if (hc > SPREAD_HCAP) {
     // neighbour tiles per axis: lane q holds entry q of the list (from the
     // table on axes of partial or few tiles)
     int rowv[3], nt[3];
@@ -1518,11 +1720,11 @@ __device__ __forceinline__ void spread_body(const PartArgs& __restrict__ p,
       const int total = __shfl_sync(0xffffffffu, incl, 31);
       for (int cbase = 0; cbase < total; cbase += 32 * SPREAD_ROUNDS) {
         int kk[SPREAD_ROUNDS];
-        short4 rr[SPREAD_ROUNDS];
+        unsigned long long rr[SPREAD_ROUNDS];
 #pragma unroll
         for (int r = 0; r < SPREAD_ROUNDS; ++r) {
           kk[r] = -1;
-          rr[r] = make_short4(0, 0, 0, 0);
+          rr[r] = 0ull;
           if (cbase + 32 * r >= total) continue;     // warp-uniform: no candidates left
           const int cidx = cbase + 32 * r + lane;
           // owning chunk lane: the first lane whose inclusive prefix exceeds cidx
@@ -1543,58 +1745,25 @@ __device__ __forceinline__ void spread_body(const PartArgs& __restrict__ p,
           if (cbase + 32 * r >= total) break;       // warp-uniform
           bool hit = false;
           if (kk[r] >= 0) {
-            const short4 rv = rr[r];
-            const int e0 = tile_offset(rv.x, lo[0], g.nx, true);
-            const int e1 = tile_offset(rv.y, lo[1], g.ny, true);
-            const int e2 = tile_offset(rv.z, lo[2], g.nz, perz);
+            const int rvx = base_x(rr[r]), rvy = base_y(rr[r]), rvz = base_z(rr[r]);
+            const int e0 = tile_offset(rvx, lo[0], g.nx, true);
+            const int e1 = tile_offset(rvy, lo[1], g.ny, true);
+            const int e2 = tile_offset(rvz, lo[2], g.nz, perz);
             hit = (shx ? e0 <= hi[0] - lo[0] && e0 + SN - 1 >= 0
-                       : axis_reach<SN>(rv.x, g.nx, true, lo[0], hi[0])) &&
+                       : axis_reach<SN>(rvx, g.nx, true, lo[0], hi[0])) &&
                   (shy ? e1 <= hi[1] - lo[1] && e1 + SN - 1 >= 0
-                       : axis_reach<SN>(rv.y, g.ny, true, lo[1], hi[1])) &&
+                       : axis_reach<SN>(rvy, g.ny, true, lo[1], hi[1])) &&
                   (shz ? e2 <= hi[2] - lo[2] && e2 + SN - 1 >= 0
-                       : axis_reach<SN>(rv.z, g.nz, perz, lo[2], hi[2]));
+                       : axis_reach<SN>(rvz, g.nz, perz, lo[2], hi[2]));
           }
           const unsigned m = __ballot_sync(0xffffffffu, hit);
           if (hit) hk[nhit + __popc(m & ((1u << lane) - 1u))] = kk[r];
           nhit += __popc(m);
         }
         __syncwarp();
-        for (int hb = 0; hb < nhit; hb += 32) {
-          const int nh = min(32, nhit - hb);
-          if (lane < nh) {
-            const StencilRecT<C>& r = recs[hk[hb + lane]];
-            SpreadHit<C>& h = stage[lane];
-            int e[3];
-            e[0] = tile_offset(r.bx, lo[0], g.nx, true);
-            e[1] = tile_offset(r.by, lo[1], g.ny, true);
-            e[2] = tile_offset(r.bz, lo[2], g.nz, perz);
-            C rw[4];
-#pragma unroll
-            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wx[q2];
-            if (shx) tile_weights_shift<SN, C>(e[0], rw, h.w[0]);
-            else tile_weights<SN, C>(r.bx, rw, g.nx, true, lo[0], h.w[0]);
-#pragma unroll
-            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wy[q2];
-            if (shy) tile_weights_shift<SN, C>(e[1], rw, h.w[1]);
-            else tile_weights<SN, C>(r.by, rw, g.ny, true, lo[1], h.w[1]);
-#pragma unroll
-            for (int q2 = 0; q2 < 4; ++q2) rw[q2] = r.wz[q2];
-            if (shz) tile_weights_shift<SN, C>(e[2], rw, h.w[2]);
-            else tile_weights<SN, C>(r.bz, rw, g.nz, perz, lo[2], h.w[2]);
-            h.F[0] = r.F[0]; h.F[1] = r.F[1]; h.F[2] = r.F[2];
-          }
-          __syncwarp();
-          for (int src = 0; src < nh; ++src) {
-            const SpreadHit<C>& h = stage[src];
-            const C wxy = h.w[0][cxl] * h.w[1][cyl];
-            const C w0 = wxy * h.w[2][czl], w1 = wxy * h.w[2][czl + 2];
-            const C f0 = h.F[0], f1 = h.F[1], f2 = h.F[2];
-            acc0[0] += w0 * f0; acc0[1] += w0 * f1; acc0[2] += w0 * f2;
-            acc1[0] += w1 * f0; acc1[1] += w1 * f1; acc1[2] += w1 * f2;
-          }
-          __syncwarp();
-        }
+        add_hits(nhit);
       }
+    }
     }
     if (in0) store_force(F, cell0, acc0[0], acc0[1], acc0[2]);
     if (in1) store_force(F, cell1, acc1[0], acc1[1], acc1[2]);

@@ -85,6 +85,53 @@ def test_coupled_steps_match_oracle(kind, order, split, n, stencil, walls, lanes
     box.close()
 
 
+FP32_SCHEMES = [("fc", 2, "base", 1, "trilinear"), ("fc", 2, "inside", 2, "trilinear"),
+                ("fc", 2, "outside", 2, "peskin4"), ("mebf", 2, "base", 1, "peskin4"),
+                ("ibm", 2, "base", 1, "peskin3"), ("fc", 1, "base", 1, "trilinear")]
+
+
+@pytest.mark.parametrize("kind,order,split,n,stencil", FP32_SCHEMES)
+@pytest.mark.parametrize("walls", [False, True])
+def test_coupled_steps_fp32_match_oracle(kind, order, split, n, stencil, walls):
+    """FP32 storage: the particle side then computes bond vectors and
+    |d|^2 - r0^2 in double-float FP32 arithmetic, stencils from a float
+    split of the FP64 positions, and the wrap tests on bit patterns.  The
+    12 x 10 x 11 box makes the chains cross the periodic faces (minimum
+    image inside the double-float bond vector).  Bounds: FP32 rounding of
+    node velocities and forces (about 1e-9 per step here); a wrong image or
+    stretch would show at 1e-4 or more.  The explicit first-order step
+    runs at a friction where it is stable (gamma h (1/m + 1/rho) < 2), so
+    rounding is not amplified from step to step."""
+    require_cuda()
+    shape = (11, 10, 12)
+    fbar0 = synth.random_populations(shape, seed=21, amp=1e-3)
+    parts = _particles(shape, kind, seed=5, nchains=3, beads=6)
+    if walls:
+        parts["pos"][:, 2] = 3.0 + np.mod(parts["pos"][:, 2], shape[0] - 6.0)
+    else:                  # put a chain across each periodic face
+        L = np.array([shape[2], shape[1], shape[0]], dtype=float)
+        parts["pos"][:6] += L - parts["pos"][:6].mean(axis=0)
+        parts["pos"] = np.mod(parts["pos"], L)
+    uw = ((0.01, 0, 0), (-0.01, 0.005, 0)) if walls else ((0, 0, 0), (0, 0, 0))
+    box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=(1e-5, 0, -1e-5),
+                        walls=walls, uw=uw, storage="f32", kind=kind, order=order,
+                        stencil=stencil, gamma=1.7 if order == 2 else 0.4, split=split, n=n,
+                        parts=parts)
+    for nsteps in (1, 2, 3):
+        box.step(nsteps)
+        for _ in range(nsteps):
+            sm.step()
+        pos, vel, fh = box.get_particles()
+        d = OC.min_image(pos - sm.parts.pos, shape, walls)
+        assert np.abs(d).max() < 1e-7, np.abs(d).max()
+        if kind != "ibm":
+            assert np.abs(vel - sm.parts.vel).max() < 1e-7
+            assert np.abs(fh - sm.last_Fh).max() < 1e-6 * max(1.0, np.abs(sm.last_Fh).max())
+    _, u = box.get_fields()
+    assert rel_l2(u, sm.fluid_velocity()) < 1e-5
+    box.close()
+
+
 @pytest.mark.parametrize("kind,order,split,n", [("fc", 2, "base", 1), ("fc", 2, "outside", 2),
                                                 ("mebf", 2, "inside", 2), ("ibm", 2, "base", 1),
                                                 ("fc", 1, "base", 1)])
