@@ -12,16 +12,20 @@
 //  * the collision runs in packed FP32 x 2 arithmetic (Blackwell's paired
 //    single-precision add, multiply and fused multiply-add), one instruction
 //    for the same operation on both cells, in the recombined form of
-//    lb_cell.cuh (BGK and MRT with fully relaxed ghosts);
+//    lb_cell.cuh (BGK and MRT with fully relaxed ghosts), and in the units
+//    of the stored values d_i = (f_i - w_i rho0) / (w_i s): the moments are
+//    sums per weight class scaled by w s, and every term of the result is
+//    formed already divided by w_i s, so no value is scaled on its way in
+//    or out;
 //  * the two results of a population are rounded stochastically to 16 bits
 //    and stored as one 32-bit word; one 32-bit random draw serves a pair of
 //    opposite populations of both cells, 8 random bits per value placed
 //    right below the last kept bit (the rounding is unbiased to within
 //    1/256 of a 16-bit spacing).
-// Every operation of the collision is the IEEE single-precision operation of
-// the one-cell form (the fused multiply-adds are written out), so the
-// results agree with it to FP32 rounding and the stochastic rounding.  Used for rows whose length is a multiple of 64 (a
-// warp covers 64 cells of one row); other boxes use the one-cell kernel.
+// The results agree with the one-cell form to a few FP32 roundings (and a
+// 16-bit spacing where such a rounding crosses a stochastic rounding step).
+// Used for rows whose length is a multiple of 64 (a warp covers 64 cells of
+// one row); other boxes use the one-cell kernel.
 #include "lb_cell.cuh"
 
 namespace lbc {
@@ -49,20 +53,6 @@ __device__ __forceinline__ f2 div2(f2 x) {
   return fma2(x, bc(hi), x * bc(lo));
 }
 
-// sum_i c_ia c_ib v_i over the compile-time velocity set (A, B in 0..2)
-template <int A, int B>
-__device__ __forceinline__ f2 csum2(const f2 (&v)[Q]) {
-  f2 s = bc(0.0f);
-  unroll_q([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr int ca = A == 0 ? cx_of(i) : (A == 1 ? cy_of(i) : cz_of(i));
-    constexpr int cb = B == 0 ? cx_of(i) : (B == 1 ? cy_of(i) : cz_of(i));
-    if constexpr (ca * cb == 1) s = s + v[i];
-    else if constexpr (ca * cb == -1) s = s - v[i];
-  });
-  return s;
-}
-
 // c_i . (x, y, z) with compile-time components
 template <int I>
 __device__ __forceinline__ f2 cdot2(f2 x, f2 y, f2 z) {
@@ -78,20 +68,12 @@ __device__ __forceinline__ f2 cdot2(f2 x, f2 y, f2 z) {
   return s;
 }
 
-// n * x for the integer weights n_i = 36 w_i (1 needs no multiply)
-template <int I>
-__device__ __forceinline__ f2 times_n(f2 x) {
-  if constexpr (n_of(I) == 1) return x;
-  else return bc(float(n_of(I))) * x;
-}
-
 // ---------------------------------------------------------------- storage
 template <typename S> struct Pair;
 template <> struct Pair<__half> {
-  // two stored values (low half: cell 2k) -> deviations times w_i s
-  __device__ static f2 unpack(uint32_t w, float ws) {
-    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
-    return f2{__fmul2_rn(v, make_float2(ws, ws))};
+  // two stored values (low half: cell 2k), as floats
+  __device__ static f2 unpack(uint32_t w) {
+    return f2{__half22float2(*reinterpret_cast<const __half2*>(&w))};
   }
   __device__ static float one(uint16_t h) { return __half2float(__ushort_as_half(h)); }
   // stochastic rounding: 8 random bits (bytes of r) added right below the
@@ -105,10 +87,9 @@ template <> struct Pair<__half> {
   }
 };
 template <> struct Pair<__nv_bfloat16> {
-  __device__ static f2 unpack(uint32_t w, float ws) {
+  __device__ static f2 unpack(uint32_t w) {
     // BF16 is the upper half of the FP32 pattern
-    const float a = __uint_as_float(w << 16), b = __uint_as_float(w & 0xFFFF0000u);
-    return f2{__fmul2_rn(make_float2(a, b), make_float2(ws, ws))};
+    return f2{make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u))};
   }
   __device__ static float one(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
   __device__ static uint32_t pack(float x0, float x1, uint32_t r0, uint32_t r1) {
@@ -141,16 +122,17 @@ struct PairDither {
 // ---------------------------------------------------------------- kernel
 constexpr int PAIR_BY = 4;      // rows per block (a warp per row, 64 cells)
 
-// stores the two values of population i, rounded with random bits (r0, r1)
-template <typename S, int I>
-__device__ __forceinline__ void put2(S* __restrict__ fout, int at, f2 v, float rsc, uint32_t r0,
-                                     uint32_t r1) {
-  const f2 x = v * bc(float(1.0 / w_of(I)) * rsc);
+// stores the two values of population i (in stored units), rounded with
+// random bits (r0, r1)
+template <typename S>
+__device__ __forceinline__ void put2(S* __restrict__ fout, int at, f2 x, uint32_t r0, uint32_t r1) {
   reinterpret_cast<uint32_t*>(fout)[at >> 1] = Pair<S>::pack(x.v.x, x.v.y, r0, r1);
 }
 
+// (BGK keeps two quadratic forms per population live: at most 80 registers
+// keep six blocks of four warps resident per SM)
 template <typename S, int COLL, bool WALLS, bool FORCED>
-__global__ void __launch_bounds__(32 * PAIR_BY, 4)
+__global__ void __launch_bounds__(32 * PAIR_BY, COLL == 0 ? 6 : 4)
 lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) {
   const Geom& g = a.g;
   const int lane = threadIdx.x;                   // blockDim.x == 32: one row per warp
@@ -182,7 +164,7 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   const int qw = qs >> 1;
   const uint32_t* w32 = reinterpret_cast<const uint32_t*>(fin);
   const uint16_t* w16 = reinterpret_cast<const uint16_t*>(fin);
-  const float sc = a.scale16;
+  const float sc = a.scale16, rsc = a.rscale16;
   const int xl = xw == 0 ? g.nx - 1 : xw - 1;            // x - 1 of the warp's first cell
   const int xr = xw + 64 == g.nx ? 0 : xw + 64;          // x + 1 of its last
 
@@ -190,12 +172,11 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   // every population loads its word and takes part in the shuffles (a
   // bounced-back population then keeps its own word), so the 19 loads can
   // all be in flight before the first shuffle waits for one
-  f2 f[Q];
+  f2 d[Q];
   unroll_q([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     constexpr int o = opp_of(i);
-    const float ws = float(w_of(i)) * sc;
     const int zs = z - cz;
     // bounced back at a wall: population opp(i) of these cells plus the
     // moving-wall term (the same for the whole warp: one z)
@@ -213,24 +194,43 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       if (lane == 31) next = (uint32_t)w16[row + xr];
       if (!bounce) v = __byte_perm(w, next, 0x5432);
     }
-    f[i] = Pair<S>::unpack(v, ws);
-    if (WALLS && cz != 0 && bounce) f[i] = f[i] + bc(rv<float>(cz > 0 ? a.bb_bot[i] : a.bb_top[i]));
+    d[i] = Pair<S>::unpack(v);
+    if (WALLS && cz != 0 && bounce)        // the moving-wall term, in stored units
+      d[i] = d[i] + bc(rv<float>(cz > 0 ? a.bb_bot[i] : a.bb_top[i]) * float(1.0 / w_of(i)) * rsc);
   });
 
-  // ---- moments, forces, velocities (as lb_cell, per lane)
-  f2 rd = f[0], jx = bc(0.0f), jy = bc(0.0f), jz = bc(0.0f);
+  // ---- moments, forces, velocities (as lb_cell, per lane).  The stored
+  // values are d_i = (f_i - w_i rho0) / (w_i s): the moments are sums per
+  // weight class (w_0; w_1..6; w_7..18) scaled by w s, and the results are
+  // formed directly in stored units (a term x n_i of the collision becomes
+  // x 36 / s), so no value is scaled on its way in or out.
+  const f2 ws0 = bc(float(w_of(0)) * sc), ws1 = bc(float(w_of(1)) * sc),
+           ws2 = bc(float(w_of(7)) * sc);
+  f2 r1 = bc(0.0f), r2 = bc(0.0f);
+  f2 jx1 = bc(0.0f), jy1 = bc(0.0f), jz1 = bc(0.0f), jx2 = bc(0.0f), jy2 = bc(0.0f), jz2 = bc(0.0f);
   unroll_q([&](auto I) {
     constexpr int i = decltype(I)::value;
-    if constexpr (i > 0) {
-      rd = rd + f[i];
-      if constexpr (cx_of(i) > 0) jx = jx + f[i];
-      if constexpr (cx_of(i) < 0) jx = jx - f[i];
-      if constexpr (cy_of(i) > 0) jy = jy + f[i];
-      if constexpr (cy_of(i) < 0) jy = jy - f[i];
-      if constexpr (cz_of(i) > 0) jz = jz + f[i];
-      if constexpr (cz_of(i) < 0) jz = jz - f[i];
+    if constexpr (i > 0 && i <= 6) {
+      r1 = r1 + d[i];
+      if constexpr (cx_of(i) > 0) jx1 = jx1 + d[i];
+      if constexpr (cx_of(i) < 0) jx1 = jx1 - d[i];
+      if constexpr (cy_of(i) > 0) jy1 = jy1 + d[i];
+      if constexpr (cy_of(i) < 0) jy1 = jy1 - d[i];
+      if constexpr (cz_of(i) > 0) jz1 = jz1 + d[i];
+      if constexpr (cz_of(i) < 0) jz1 = jz1 - d[i];
+    } else if constexpr (i > 6) {
+      r2 = r2 + d[i];
+      if constexpr (cx_of(i) > 0) jx2 = jx2 + d[i];
+      if constexpr (cx_of(i) < 0) jx2 = jx2 - d[i];
+      if constexpr (cy_of(i) > 0) jy2 = jy2 + d[i];
+      if constexpr (cy_of(i) < 0) jy2 = jy2 - d[i];
+      if constexpr (cz_of(i) > 0) jz2 = jz2 + d[i];
+      if constexpr (cz_of(i) < 0) jz2 = jz2 - d[i];
     }
   });
+  const f2 rd = fma2(ws2, r2, fma2(ws1, r1, ws0 * d[0]));
+  const f2 jx = fma2(ws2, jx2, ws1 * jx1), jy = fma2(ws2, jy2, ws1 * jy1),
+           jz = fma2(ws2, jz2, ws1 * jz1);
   const f2 rho = bc(rv<float>(a.rho0)) + rd;
   if (!isfinite(rho.v.x) || !isfinite(rho.v.y)) atomicOr(a.health, 1);
   const f2 inv = mk2(1.0f / rho.v.x, 1.0f / rho.v.y);
@@ -263,44 +263,61 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
   const f2 uu1 = div2<24>(fma2(u1z, u1z, fma2(u1y, u1y, u1x * u1x)));
   const f2 c18 = bc(0.125f);
   auto quad = [&](f2 cu, f2 uu) { return fma2(cu * cu, c18, bc(0.0f) - uu); };
-  const float rsc = a.rscale16;
+  const f2 k36 = bc(36.0f * rsc), k3 = bc(3.0f * rsc);    // n_i / (w_i s), n_i / (12 w_i s)
+  const f2 rho36 = k36 * rho;
 
   if constexpr (COLL == 0) {
     // BGK: f*_i = gamma fbar_i + n_i [ (1-gamma) rd/36 + c_i.((1-gamma) j + F)/12
     //                                  + rho (Q_i(u1) - gamma Q_i(u0)) ]
     const float gam = rv<float>(a.gamma_bgk);
     const f2 g2 = bc(gam), ng2 = bc(-gam), om2 = bc(1.0f - gam);
-    const f2 sm = div2<36>(om2 * rd);
-    const f2 qx = div2<12>(fma2(om2, jx, Fx)), qy = div2<12>(fma2(om2, jy, Fy)),
-             qz = div2<12>(fma2(om2, jz, Fz));
+    const f2 sm36 = bc((1.0f - gam) * rsc) * rd;
+    const f2 qx = k3 * fma2(om2, jx, Fx), qy = k3 * fma2(om2, jy, Fy), qz = k3 * fma2(om2, jz, Fz);
     {
-      const f2 E = times_n<0>(fma2(rho, fma2(ng2, bc(0.0f) - uu0, bc(0.0f) - uu1), sm));
+      const f2 E = fma2(rho36, fma2(ng2, bc(0.0f) - uu0, bc(0.0f) - uu1), sm36);
       const uint32_t r = dz(0);
-      put2<S, 0>(fout, cell, fma2(g2, f[0], E), rsc, r, r >> 8);
+      put2<S>(fout, cell, fma2(g2, d[0], E), r, r >> 8);
     }
     unroll_pairs([&](auto I) {
       constexpr int i = decltype(I)::value;
       const f2 q0 = quad(cdot2<i>(u0x, u0y, u0z), uu0);
       const f2 q1 = quad(cdot2<i>(u1x, u1y, u1z), uu1);
-      const f2 E = times_n<i>(fma2(rho, fma2(ng2, q0, q1), sm));
-      const f2 O = times_n<i>(cdot2<i>(qx, qy, qz));
+      const f2 E = fma2(rho36, fma2(ng2, q0, q1), sm36);
+      const f2 O = cdot2<i>(qx, qy, qz);
       const uint32_t r = dz(i);
-      put2<S, i>(fout, i * qs + cell, fma2(g2, f[i], E + O), rsc, r, r >> 8);
-      put2<S, i + 1>(fout, (i + 1) * qs + cell, fma2(g2, f[i + 1], E - O), rsc, r >> 16, r >> 24);
+      put2<S>(fout, i * qs + cell, fma2(g2, d[i], E + O), r, r >> 8);
+      put2<S>(fout, (i + 1) * qs + cell, fma2(g2, d[i + 1], E - O), r >> 16, r >> 24);
     });
   } else {
     // MRT with both ghost groups fully relaxed: the bulk and shear moments
-    // from the non-equilibrium stress (as lb_cell, COLL 2)
+    // from the non-equilibrium stress (as lb_cell, COLL 2).  Second moments
+    // sum_i c_ia c_ib f_i per weight class: the +-a pair of w_1 on the
+    // diagonal, the w_7..18 populations with c_ia c_ib = +-1
+    auto second = [&](auto A, auto B) {
+      constexpr int ia = decltype(A)::value, ib = decltype(B)::value;
+      f2 s1 = bc(0.0f), s2 = bc(0.0f);
+      unroll_q([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ca = ia == 0 ? cx_of(i) : (ia == 1 ? cy_of(i) : cz_of(i));
+        constexpr int cb = ib == 0 ? cx_of(i) : (ib == 1 ? cy_of(i) : cz_of(i));
+        if constexpr (i > 0 && i <= 6 && ca * cb == 1) s1 = s1 + d[i];
+        if constexpr (i > 6 && ca * cb == 1) s2 = s2 + d[i];
+        if constexpr (i > 6 && ca * cb == -1) s2 = s2 - d[i];
+      });
+      if constexpr (ia == ib) return fma2(ws2, s2, ws1 * s1);
+      else return ws2 * s2;
+    };
     const f2 nrho = bc(0.0f) - rho;
     const f2 r3 = div2<3>(rd);
-    const f2 nxx = fma2(nrho * u0x, u0x, csum2<0, 0>(f) - r3);
-    const f2 nyy = fma2(nrho * u0y, u0y, csum2<1, 1>(f) - r3);
-    const f2 nzz = fma2(nrho * u0z, u0z, csum2<2, 2>(f) - r3);
-    const f2 nxy = fma2(nrho * u0x, u0y, csum2<0, 1>(f));
-    const f2 nyz = fma2(nrho * u0y, u0z, csum2<1, 2>(f));
-    const f2 nxz = fma2(nrho * u0x, u0z, csum2<0, 2>(f));
+    const f2 nxx = fma2(nrho * u0x, u0x, second(IC<0>{}, IC<0>{}) - r3);
+    const f2 nyy = fma2(nrho * u0y, u0y, second(IC<1>{}, IC<1>{}) - r3);
+    const f2 nzz = fma2(nrho * u0z, u0z, second(IC<2>{}, IC<2>{}) - r3);
+    const f2 nxy = fma2(nrho * u0x, u0y, second(IC<0>{}, IC<1>{}));
+    const f2 nyz = fma2(nrho * u0y, u0z, second(IC<1>{}, IC<2>{}));
+    const f2 nxz = fma2(nrho * u0x, u0z, second(IC<0>{}, IC<2>{}));
     const f2 tr = nxx + nyy + nzz;
-    const float gb = rv<float>(a.gamma_k[0]), gs = rv<float>(a.gamma_k[1]);
+    // the moments after relaxation, times 1/s (w_i post / (w_i s))
+    const float gb = rv<float>(a.gamma_k[0]) * rsc, gs = rv<float>(a.gamma_k[1]) * rsc;
     f2 m[10];
     m[4] = tr * bc(gb * float(1.0 / mrt_b(4)));
     m[5] = fma2(bc(3.0f), nxx, bc(0.0f) - tr) * bc(gs * float(1.0 / mrt_b(5)));
@@ -308,8 +325,8 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
     m[7] = nxy * bc(gs * float(1.0 / mrt_b(7)));
     m[8] = nyz * bc(gs * float(1.0 / mrt_b(8)));
     m[9] = nxz * bc(gs * float(1.0 / mrt_b(9)));
-    const f2 md = div2<36>(rd);
-    const f2 j1x = div2<12>(jx + Fx), j1y = div2<12>(jy + Fy), j1z = div2<12>(jz + Fz);
+    const f2 md36 = bc(rsc) * rd;                          // 36 rd / (36 s)
+    const f2 j1x = k3 * (jx + Fx), j1y = k3 * (jy + Fy), j1z = k3 * (jz + Fz);
     auto even = [&](auto I) {
       constexpr int i = decltype(I)::value;
       f2 post = bc(0.0f);
@@ -321,20 +338,20 @@ lb_pair_kernel(const S* __restrict__ fin, S* __restrict__ fout, const LBArgs a) 
       };
       acc(mrt_e(4, i), m[4]); acc(mrt_e(5, i), m[5]); acc(mrt_e(6, i), m[6]);
       acc(mrt_e(7, i), m[7]); acc(mrt_e(8, i), m[8]); acc(mrt_e(9, i), m[9]);
-      const f2 eq = times_n<i>(fma2(rho, quad(cdot2<i>(u1x, u1y, u1z), uu1), md));
-      return any ? fma2(bc(float(w_of(i))), post, eq) : eq;
+      const f2 eq = fma2(rho36, quad(cdot2<i>(u1x, u1y, u1z), uu1), md36);
+      return any ? post + eq : eq;
     };
     {
       const uint32_t r = dz(0);
-      put2<S, 0>(fout, cell, even(IC<0>{}), rsc, r, r >> 8);
+      put2<S>(fout, cell, even(IC<0>{}), r, r >> 8);
     }
     unroll_pairs([&](auto I) {
       constexpr int i = decltype(I)::value;
       const f2 E = even(I);
-      const f2 O = times_n<i>(cdot2<i>(j1x, j1y, j1z));
+      const f2 O = cdot2<i>(j1x, j1y, j1z);
       const uint32_t r = dz(i);
-      put2<S, i>(fout, i * qs + cell, E + O, rsc, r, r >> 8);
-      put2<S, i + 1>(fout, (i + 1) * qs + cell, E - O, rsc, r >> 16, r >> 24);
+      put2<S>(fout, i * qs + cell, E + O, r, r >> 8);
+      put2<S>(fout, (i + 1) * qs + cell, E - O, r >> 16, r >> 24);
     });
   }
 }

@@ -1585,10 +1585,25 @@ __device__ __forceinline__ void spread_body(const PartArgs& __restrict__ p,
     whole[d] = n3[d] % TILE == 0 && (!(d < 2 || perz) || ntv[d] >= 3);
   const int stride = nblk * WARPS;
   int j = bid * WARPS + wid;
+  // software pipeline over the warp's tiles: the list entry two tiles
+  // ahead, and the hit list (count and entries) of the next tile, are
+  // loaded while this one is spread
   int4 lt_next = j < nlive ? a.live_tiles[j] : make_int4(0, 0, 0, 0);
+  int4 lt_next2 = j + stride < nlive ? a.live_tiles[j + stride] : make_int4(0, 0, 0, 0);
+  uint32_t hc_next = 0u, key_next = 0u;
+  if (a.hcnt != nullptr && j < nlive) {
+    hc_next = a.hcnt[lt_next.x];
+    key_next = a.hits[(size_t)lt_next.x * SPREAD_HCAP + lane];
+  }
   for (; j < nlive; j += stride) {
     const int4 lt = lt_next;
-    if (j + stride < nlive) lt_next = a.live_tiles[j + stride];   // next tile, ahead of use
+    const uint32_t hc_cur = hc_next, key_cur = key_next;
+    lt_next = lt_next2;
+    if (j + 2 * stride < nlive) lt_next2 = a.live_tiles[j + 2 * stride];
+    if (a.hcnt != nullptr && j + stride < nlive) {
+      hc_next = a.hcnt[lt_next.x];
+      key_next = a.hits[(size_t)lt_next.x * SPREAD_HCAP + lane];
+    }
     const int t = lt.x;
     const int tt[3] = {lt.y, lt.z, lt.w};
     const int lo[3] = {tt[0] * TILE, tt[1] * TILE, tt[2] * TILE};
@@ -1646,8 +1661,8 @@ __device__ __forceinline__ void spread_body(const PartArgs& __restrict__ p,
     // fixed order; a list that overflowed (or none) takes the search below
     int hc = SPREAD_HCAP + 1;
     if (a.hcnt != nullptr) {
-      hc = (int)a.hcnt[t];
-      uint32_t key = a.hits[(size_t)t * SPREAD_HCAP + lane];
+      hc = (int)hc_cur;
+      uint32_t key = key_cur;
       if (hc <= SPREAD_HCAP) {
         if (lane >= hc) key = 0xFFFFFFFFu;
 #pragma unroll
