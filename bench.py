@@ -379,7 +379,7 @@ def other_workload_boxes(name, storage, stencil=None, kind=None, mass_scale=1.0)
     return box, nx * ny * nz, desc
 
 
-OTHER_WORKLOADS = (("ibm_shells_192", ("f32", "bf16dev")),
+OTHER_WORKLOADS = (("ibm_shells_192", ("f32", "f16dev", "bf16dev")),
                    ("mebf_rigid_spheres_128", ("f32", "f32_trilinear")))
 
 

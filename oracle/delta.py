@@ -82,7 +82,8 @@ def stencil(pos, shape, kind, walls=False):
     flat = (iz[:, :, None, None] * ny + iy[:, None, :, None]) * nx + ix[:, None, None, :]
     wt = wz[:, :, None, None] * wy[:, None, :, None] * wx[:, None, None, :]
     M = pos.shape[0]
-    return flat.reshape(M, -1), wt.reshape(M, -1)
+    nn = WINDOW.size ** 3
+    return flat.reshape(M, nn), wt.reshape(M, nn)
 
 
 def interpolate(field, pos, kind, walls=False):

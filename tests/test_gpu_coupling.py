@@ -326,3 +326,54 @@ def test_single_block_and_multi_pass_sorts(M):
     assert box.status() == 0
     tile0 = np.floor(OC.wrap_positions(pos, shape, False) / 4.0)
     assert (np.floor(pos_g / 4.0) != tile0).any(axis=1).sum() > 100   # re-binned markers
+
+
+@pytest.mark.parametrize("storage,stencil", [("f64", "trilinear"), ("f32", "trilinear"),
+                                             ("f64", "peskin4"), ("f32", "peskin3")])
+def test_long_axis_beyond_16_bit_stencil_bases(storage, stencil):
+    """A 40000 x 4 x 4 box: stencil bases beyond 2^15 along x (kept as
+    21-bit fields), markers on an exact node, at half-integers, around 2^15
+    and across the periodic face, against the oracle.  The 4-cell axes fold
+    the stencils onto themselves."""
+    require_cuda()
+    shape = (4, 4, 40000)
+    fbar0 = synth.random_populations(shape, seed=3, amp=1e-3)
+    pos = np.array([[0.0, 1.3, 2.2], [39999.5, 2.0, 0.5], [39999.9, 3.7, 1.1],
+                    [20000.25, 0.2, 3.9], [32767.5, 1.5, 2.5], [32768.5, 2.5, 1.5],
+                    [39000.0, 1.0, 1.0]])
+    rng = np.random.default_rng(7)
+    parts = dict(pos=pos, vel=0.01 * rng.standard_normal(pos.shape), mass=np.ones(len(pos)))
+    box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=(1e-5, 0, 0), storage=storage,
+                        kind="fc", stencil=stencil, gamma=1.0, parts=parts)
+    tol = 1e-11 if storage == "f64" else 1e-7
+    for _ in range(2):
+        box.step(1)
+        sm.step()
+        p, v, fh = box.get_particles()
+        assert np.abs(OC.min_image(p - sm.parts.pos, shape, False)).max() < tol
+        assert np.abs(v - sm.parts.vel).max() < tol
+        assert np.abs(fh - sm.last_Fh).max() < tol
+    _, u = box.get_fields()
+    assert rel_l2(u, sm.fluid_velocity()) < (1e-10 if storage == "f64" else 1e-5)
+    box.close()
+
+
+def test_coupled_box_without_particles_is_the_fluid_step():
+    """A force-coupled box whose particle set is empty steps the fluid alone
+    (second order: the body force's half steps), as the oracle without
+    coupling does."""
+    require_cuda()
+    shape = (6, 7, 9)
+    fbar0 = synth.random_populations(shape, seed=4, amp=1e-3)
+    box, sm = make_pair(shape, fbar0, coll="bgk", tau=0.9, g=(2e-5, -1e-5, 0), storage="f64",
+                        kind="fc", stencil="peskin4", gamma=1.0,
+                        parts=dict(pos=np.zeros((0, 3)), vel=np.zeros((0, 3)), mass=np.ones(0)))
+    _, ref = make_pair(shape, fbar0, coll="bgk", tau=0.9, g=(2e-5, -1e-5, 0), storage="f64")
+    box.step(3)
+    for _ in range(3):
+        ref.step()
+    assert box.nparticles == 0
+    assert np.abs(box.get_populations() - ref.fbar).max() < 1e-13
+    _, _, st = box.invariants()
+    assert st == 0
+    box.close()

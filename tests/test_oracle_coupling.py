@@ -275,3 +275,24 @@ def test_literal_and_recombined_lb_give_same_trajectories(kind, rng):
     assert np.abs(a.fbar - b.fbar).max() < 1e-15
     assert np.abs(a.parts.pos - b.parts.pos).max() < 1e-13
     assert np.abs(a.parts.vel - b.parts.vel).max() < 1e-15
+
+
+@pytest.mark.parametrize("kind,order", [("fc", 2), ("fc", 1), ("mebf", 2), ("ebf", 2), ("ibm", 2),
+                                        ("ibm", 1)])
+def test_empty_particle_set_is_the_fluid_step(kind, order):
+    """Degenerate case: with no particles every coupling operator is the
+    identity and spreads nothing, so the coupled step is the fluid step with
+    its body force, bit for bit."""
+    shape = (6, 7, 9)
+    rng = np.random.default_rng(4)
+    fbar = L.equilibrium(np.ones(shape), np.zeros((3,) + shape)) * (1.0 + 1e-3 * rng.standard_normal((19,) + shape))
+    p = lb.LBParams(collision="mrt", tau=0.9, body_force=(2e-5, -1e-5, 0.0))
+    parts = CP.Particles(np.zeros((0, 3)), vel=np.zeros((0, 3)), mass=np.ones(0))
+    sm = S.Sim(shape, p, S.CouplingParams(kind, order, "peskin4", gamma=1.0), parts,
+                fbar=fbar.copy())
+    ref = S.Sim(shape, p, S.CouplingParams("none", order, "trilinear"), None, fbar=fbar.copy())
+    for _ in range(3):
+        sm.step()
+        ref.step()
+    assert np.array_equal(sm.fbar, ref.fbar)
+    assert sm.parts.pos.shape == (0, 3)
