@@ -196,6 +196,41 @@ def test_immersion_limit_converges_on_a_box(rng):
     assert np.abs(Fh + fint).max() < 1e-6
 
 
+def test_heavy_particle_limit_is_the_original_ebf(rng):
+    """The other end of the immersion number (Sec. 5.3, Eq. [immersion]):
+    m >> rho a^3 gives r -> 0, and the modified EBF becomes the original
+    EBF of Eq. [ebf] (gamma = rho a^3 / h, intrinsic forces on the particles
+    only), here the explicit first-order forms of both on a grid with bonds
+    and a body force: differences shrink like 1/m."""
+    shape = (6, 7, 8)
+    u = np.zeros((3,) + shape)
+    u[0] = 0.01 * np.sin(2 * np.pi * np.arange(6) / 6)[:, None, None]
+    f0 = L.equilibrium(np.ones(shape), u)
+    pos0 = rng.uniform(0, 6, (4, 3))
+    vel0 = 0.01 * rng.standard_normal((4, 3))
+    bonds = [[0, 1], [1, 2], [2, 3]]
+
+    def run(kind, m):
+        p = lb.LBParams(tau=0.8, body_force=(1e-5, 0.0, 0.0))
+        parts = CP.Particles(pos0.copy(), vel=vel0.copy(), mass=np.full(4, m), bonds=bonds,
+                             bond_k=0.05, bond_r0=1.0)
+        sm = S.Sim(shape, p, S.CouplingParams(kind, 1, "trilinear"), parts, fbar=f0.copy())
+        for _ in range(6):
+            sm.step()
+        return sm
+
+    ref_last = None
+    diffs = []
+    for m in (1e5, 1e6, 1e7):
+        a, b = run("mebf", m), run("ebf", m)
+        d = max(np.abs(a.fbar - b.fbar).max(), np.abs(a.parts.vel - b.parts.vel).max(),
+                np.abs(CP.min_image(a.parts.pos - b.parts.pos, shape, False)).max())
+        diffs.append(d)
+        ref_last = d
+    assert ref_last < 1e-8, diffs
+    assert 5 < diffs[0] / diffs[1] < 20 and 5 < diffs[1] / diffs[2] < 20, diffs
+
+
 def test_ibm_uniform_acceleration():
     """Body force g on a periodic box: u_phys(t) = u_phys(0) + g t exactly, so
     the trapezoidal IBM update is exact and the first-order one lags by
