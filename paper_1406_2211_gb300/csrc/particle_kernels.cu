@@ -13,13 +13,18 @@
 // Eqs. [ebf], [modified-ebf]).  Positions and velocities are integrated in
 // FP64; forces and the coupling arithmetic use the compute type C of the
 // population storage (double for FP64 storage, float otherwise), because
-// FP64 arithmetic is a small fraction of the FP32 rate on this GPU.
+// FP64 arithmetic is a small fraction of the FP32 rate on this GPU.  With
+// FP32 compute, bond vectors, stencil bases and wrap tests are taken from
+// the FP64 state without FP64 work (particle_device.cuh: split_df).
 //
 // Spreading is a gather over force tiles of 4^3 cells: one warp owns one
-// live tile, tests the markers binned into the neighbouring tiles with a
-// cheap reach test on their stencil base (ballot), and adds the survivors one
-// after another into per-lane register sums (each lane owns two cells of the
-// tile), so no atomics are used and the summation order is fixed (markers
+// live tile and adds the markers whose stencil reaches it one after another
+// into per-lane register sums (each lane owns two cells of the tile), so no
+// atomics touch the force field and the summation order is fixed.  The
+// markers come from the tile's hit list, appended by the gather and sorted
+// by slot in the warp (trilinear stencils, up to 32 per tile), or else from
+// a search of the markers binned into the neighbouring tiles with a cheap
+// reach test on their stencil base (ballot), in candidate order (markers
 // sorted by tile, tiles in a fixed order).
 //
 // Markers are binned once per step; the bins stay valid while a marker is
