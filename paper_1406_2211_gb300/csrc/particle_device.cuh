@@ -1225,45 +1225,146 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
       break;
   }
   if (a.rec && (a.mode == GM_COUPLE || a.mode == GM_IBM_HALF || a.mode == GM_IBM1)) {
-    unsigned long long claimed = 0ull;   // bit (qz SN + qy) SN + qx
-    int nclaim = 0;
-    int tq[3][SN];
-    {
-      if (sub == 0) {
-        StencilRecT<C> r;
-        r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
-        for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
-        r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
-        r.pad = C(0);
-        static_cast<StencilRecT<C>*>(a.rec)[k] = r;
-        a.reach[k] = pack_base(b[0], b[1], b[2]);
-      }
-      // claim the tiles the stencil reaches (nodes with non-zero weight); per
-      // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
-      // node's tile or carries no weight
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int q = 0; q < SN; ++q) {
-          int t = -1;
-          if (w[c][q] != C(0)) {
-            int node = b[c] + q;
-            if (per[c]) node = wrap_int(node, n3[c]);
-            if (node >= 0 && node < n3[c]) t = node >> TILE_SHIFT;
-          }
-#pragma unroll
-          for (int e = 0; e < q; ++e) if (tq[c][e] == t) t = -1;
-          tq[c][q] = t;
+    if constexpr (SN == 2) {
+      // trilinear: the 2 x 2 x 2 node combinations, unrolled
+      unsigned long long claimed = 0ull;   // bit (qz SN + qy) SN + qx
+      int nclaim = 0;
+      int tq[3][SN];
+      {
+        if (sub == 0) {
+          StencilRecT<C> r;
+          r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
+          for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
+          r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
+          r.pad = C(0);
+          static_cast<StencilRecT<C>*>(a.rec)[k] = r;
+          a.reach[k] = pack_base(b[0], b[1], b[2]);
         }
-      }
+        // claim the tiles the stencil reaches (nodes with non-zero weight); per
+        // axis tq[c][q] is the tile of node q, or -1 if it repeats an earlier
+        // node's tile or carries no weight
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int q = 0; q < SN; ++q) {
+            int t = -1;
+            if (w[c][q] != C(0)) {
+              int node = b[c] + q;
+              if (per[c]) node = wrap_int(node, n3[c]);
+              if (node >= 0 && node < n3[c]) t = node >> TILE_SHIFT;
+            }
+#pragma unroll
+            for (int e = 0; e < q; ++e) if (tq[c][e] == t) t = -1;
+            tq[c][q] = t;
+          }
+        }
+#pragma unroll
+        for (int qz = 0; qz < SN; ++qz)
+#pragma unroll
+          for (int qy = 0; qy < SN; ++qy)
+#pragma unroll
+            for (int qx = 0; qx < SN; ++qx)
+              if (qz % GL == sub && tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
+                const int tile = (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
+                bool first;
+                if (a.hcnt != nullptr) {
+                  // the marker joins the tile's hit list; the first to join
+                  // claims the tile
+                  const uint32_t slot = atomicAdd(a.hcnt + tile, 1u);
+                  if (slot < (uint32_t)SPREAD_HCAP)
+                    a.hits[(size_t)tile * SPREAD_HCAP + slot] = (uint32_t)k;
+                  first = slot == 0u;
+                  if (first) a.mark[tile] = 1u;
+                } else {
+                  // most tiles are claimed already: an L2 read (marks only go
+                  // from 0 to 1 during the gather) spares their atomic
+                  uint32_t* m = a.mark + tile;
+                  first = __ldcg(m) == 0u && atomicExch(m, 1u) == 0u;
+                }
+                if (first) {
+                  claimed |= 1ull << ((qz * SN + qy) * SN + qx);
+                  ++nclaim;
+                }
+              }
+        if (a.keys && sub == 0) {
+          // the bins are valid while every stencil node lies within three
+          // cells of the home tile (the reach of the spreading's neighbour
+          // search)
+          const int t = home;
+          const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+          bool ok = true;
+          for (int c = 0; c < 3; ++c) {
+            const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
+            ok = ok && stencil_near_home<SN>(b[c], lo, hi, n3[c], per[c]);
+          }
+          if (!ok) *a.status = 1;
+        }
+    }
+      // list slots for the claimed tiles, one atomic per warp
+      int incl = nclaim;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(am, incl, off);
+        if (lane >= off) incl += u;
+    }
+      const int total = __shfl_sync(am, incl, nact - 1);
+      int base = 0;
+      if (lane == nact - 1 && total > 0) base = atomicAdd(a.nlive, total);
+      base = __shfl_sync(am, base, nact - 1) + incl - nclaim;
 #pragma unroll
       for (int qz = 0; qz < SN; ++qz)
 #pragma unroll
         for (int qy = 0; qy < SN; ++qy)
 #pragma unroll
           for (int qx = 0; qx < SN; ++qx)
-            if (qz % GL == sub && tq[2][qz] >= 0 && tq[1][qy] >= 0 && tq[0][qx] >= 0) {
-              const int tile = (tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx];
+            if (claimed & (1ull << ((qz * SN + qy) * SN + qx)))
+              a.live_tiles[base++] = make_int4((tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx],
+                                               tq[0][qx], tq[1][qy], tq[2][qz]);
+    } else {
+      // 4- and 3-point stencils: loops over the distinct tiles per axis
+      // instead of the SN^3 node combinations
+      // per axis the distinct tiles of the nodes with non-zero weight, in
+      // node order (at most three: a partial last tile and the periodic wrap)
+      int tl[3][3], ntl[3];
+      uint32_t claimed = 0u;               // bit of the tile combination cid
+      int nclaim = 0;
+      {
+        if (sub == 0) {
+          StencilRecT<C> r;
+          r.bx = b[0]; r.by = b[1]; r.bz = b[2]; r.kind = ST;
+          for (int q = 0; q < 4; ++q) { r.wx[q] = w[0][q]; r.wy[q] = w[1][q]; r.wz[q] = w[2][q]; }
+          r.F[0] = Frec[0]; r.F[1] = Frec[1]; r.F[2] = Frec[2];
+          r.pad = C(0);
+          static_cast<StencilRecT<C>*>(a.rec)[k] = r;
+          a.reach[k] = pack_base(b[0], b[1], b[2]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          ntl[c] = 0;
+          tl[c][0] = tl[c][1] = tl[c][2] = -1;
+#pragma unroll
+          for (int q = 0; q < SN; ++q) {
+            if (w[c][q] == C(0)) continue;
+            int node = b[c] + q;
+            if (per[c]) node = wrap_int(node, n3[c]);
+            if (node < 0 || node >= n3[c]) continue;
+            const int t = node >> TILE_SHIFT;
+            if (t == tl[c][0] || t == tl[c][1] || t == tl[c][2]) continue;
+            if (ntl[c] == 0) tl[c][0] = t;
+            else if (ntl[c] == 1) tl[c][1] = t;
+            else tl[c][2] = t;
+            ++ntl[c];
+          }
+        }
+        // claim the tiles the stencil reaches: the combinations of the axes'
+        // tiles, shared out over the marker's lanes
+        int cid = 0;
+        for (int iz = 0; iz < ntl[2]; ++iz)
+          for (int iy = 0; iy < ntl[1]; ++iy)
+            for (int ix = 0; ix < ntl[0]; ++ix, ++cid) {
+              if (cid % GL != sub) continue;
+              const int tx = pick(tl[0], ix), ty = pick(tl[1], iy), tz = pick(tl[2], iz);
+              const int tile = (tz * g.nty + ty) * g.ntx + tx;
               bool first;
               if (a.hcnt != nullptr) {
                 // the marker joins the tile's hit list; the first to join
@@ -1280,44 +1381,46 @@ __device__ __forceinline__ void gather_body(const PartArgs& __restrict__ p,
                 first = __ldcg(m) == 0u && atomicExch(m, 1u) == 0u;
               }
               if (first) {
-                claimed |= 1ull << ((qz * SN + qy) * SN + qx);
+                claimed |= 1u << cid;
                 ++nclaim;
               }
             }
-      if (a.keys && sub == 0) {
-        // the bins are valid while every stencil node lies within three
-        // cells of the home tile (the reach of the spreading's neighbour
-        // search)
-        const int t = home;
-        const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
-        bool ok = true;
-        for (int c = 0; c < 3; ++c) {
-          const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
-          ok = ok && stencil_near_home<SN>(b[c], lo, hi, n3[c], per[c]);
+        if (a.keys && sub == 0) {
+          // the bins are valid while every stencil node lies within three
+          // cells of the home tile (the reach of the spreading's neighbour
+          // search)
+          const int t = home;
+          const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+          bool ok = true;
+          for (int c = 0; c < 3; ++c) {
+            const int lo = tt[c] * TILE, hi = min(lo + TILE, n3[c]) - 1;
+            ok = ok && stencil_near_home<SN>(b[c], lo, hi, n3[c], per[c]);
+          }
+          if (!ok) *a.status = 1;
         }
-        if (!ok) *a.status = 1;
-      }
     }
-    // list slots for the claimed tiles, one atomic per warp
-    int incl = nclaim;
+      // list slots for the claimed tiles, one atomic per warp
+      int incl = nclaim;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int u = __shfl_up_sync(am, incl, off);
-      if (lane >= off) incl += u;
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(am, incl, off);
+        if (lane >= off) incl += u;
     }
-    const int total = __shfl_sync(am, incl, nact - 1);
-    int base = 0;
-    if (lane == nact - 1 && total > 0) base = atomicAdd(a.nlive, total);
-    base = __shfl_sync(am, base, nact - 1) + incl - nclaim;
-#pragma unroll
-    for (int qz = 0; qz < SN; ++qz)
-#pragma unroll
-      for (int qy = 0; qy < SN; ++qy)
-#pragma unroll
-        for (int qx = 0; qx < SN; ++qx)
-          if (claimed & (1ull << ((qz * SN + qy) * SN + qx)))
-            a.live_tiles[base++] = make_int4((tq[2][qz] * g.nty + tq[1][qy]) * g.ntx + tq[0][qx],
-                                             tq[0][qx], tq[1][qy], tq[2][qz]);
+      const int total = __shfl_sync(am, incl, nact - 1);
+      int base = 0;
+      if (lane == nact - 1 && total > 0) base = atomicAdd(a.nlive, total);
+      base = __shfl_sync(am, base, nact - 1) + incl - nclaim;
+      if (claimed != 0u) {
+        int cid2 = 0;
+        for (int iz = 0; iz < ntl[2]; ++iz)
+          for (int iy = 0; iy < ntl[1]; ++iy)
+            for (int ix = 0; ix < ntl[0]; ++ix, ++cid2)
+              if (claimed & (1u << cid2)) {
+                const int tx = pick(tl[0], ix), ty = pick(tl[1], iy), tz = pick(tl[2], iz);
+                a.live_tiles[base++] = make_int4((tz * g.nty + ty) * g.ntx + tx, tx, ty, tz);
+              }
+    }
+    }
   }
 }
 
