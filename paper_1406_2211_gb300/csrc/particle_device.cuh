@@ -123,6 +123,30 @@ __device__ inline float two_sum(float a, float b, float& err) {
   return s;
 }
 
+// Double-float arithmetic (value h + l, |l| <= ulp(h) / 2) on the FP32 pipe
+struct dflt {
+  float h, l;
+};
+__device__ inline dflt df_add(dflt a, dflt b) {
+  float e;
+  const float s = two_sum(a.h, b.h, e);
+  e += a.l + b.l;
+  const float h = s + e;
+  return dflt{h, e - (h - s)};
+}
+__device__ inline dflt df_mul(dflt a, dflt b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);                 // exact residue of the product
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  const float h = p + e;
+  return dflt{h, e - (h - p)};
+}
+__device__ inline dflt df_of(double x) {
+  dflt r;
+  split_df(x, r.h, r.l);
+  return r;
+}
+
 // A stencil base (x, y, z), each in -2^20 .. 2^20 - 1, as three signed
 // 21-bit fields of one 64-bit word (bits 0-20, 22-42, 43-63)
 __device__ inline unsigned long long pack_base(int x, int y, int z) {
@@ -206,6 +230,47 @@ __device__ inline bool near_home(const Geom& g, uint32_t home, const double (&r)
       else if (dd >= h) dd -= n3[c];
     }
     inside = inside && dd >= -0.5 && dd < (double)w + 0.5;
+  }
+  return inside;
+}
+
+// The same two decisions from the float splits of the coordinates (FP32
+// compute: no FP64 work).  floor(x) is exact for |x| < 2^24; the home test
+// may differ from the FP64 one within float rounding of the half-cell
+// margins, which only moves a re-binning by a step.
+__device__ inline int floor_df(double x) {
+  float h, l;
+  split_df(x, h, l);
+  float fl = floorf(h);
+  if (fl == h && l < 0.0f) fl -= 1.0f;
+  return (int)fl;
+}
+__device__ inline uint32_t key_of_f(const Geom& g, double x, double y, double z) {
+  int ix = wrap_int(floor_df(x), g.nx), iy = wrap_int(floor_df(y), g.ny);
+  int iz = floor_df(z);
+  if (g.walls) iz = iz < 0 ? 0 : (iz >= g.nz ? g.nz - 1 : iz);
+  else iz = wrap_int(iz, g.nz);
+  return (uint32_t)tile_of(g, ix, iy, iz);
+}
+__device__ inline bool near_home_f(const Geom& g, uint32_t home, const double (&r)[3]) {
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const bool per[3] = {true, true, !g.walls};
+  const int t = (int)home;
+  const int tt[3] = {t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty)};
+  bool inside = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int lo = tt[c] * TILE, w = min(lo + TILE, n3[c]) - lo;
+    if (per[c] && n3[c] <= 3 * TILE) continue;      // the search covers the axis
+    float h, l;
+    split_df(r[c], h, l);
+    float dd = (h - (float)lo) + l;
+    if (per[c]) {
+      const float hn = 0.5f * n3[c];
+      if (dd < -hn) dd += n3[c];
+      else if (dd >= hn) dd -= n3[c];
+    }
+    inside = inside && dd >= -0.5f && dd < (float)w + 0.5f;
   }
   return inside;
 }
@@ -339,13 +404,33 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
       const float inv_nf = F32 ? 1.0f / (float)cnt : 0.0f;
       const double inv_n = F32 ? 0.0 : 1.0 / (double)cnt;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double site = fr[c] + fr[3 + 3 * c] * q[0] + fr[4 + 3 * c] * q[1] + fr[5 + 3 * c] * q[2];
-        const double dev = min_image(r1[c] - site, n3[c], per[c]);
-        if (F32)
-          F[c] += (C)(-d.rigid.k * dev) + (C)d.rigid.frep[3 * body + c] * (C)inv_nf;
-        else
+      if constexpr (F32) {
+        // dev = (r1 - X_b) - R q in double-float arithmetic (FP32 pipe)
+        const dflt qd[3] = {df_of(q[0]), df_of(q[1]), df_of(q[2])};
+        const float kf = (float)d.rigid.k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dflt e = df_add(df_of(r1[c]), dflt{0.0f, 0.0f});
+          const dflt xb = df_of(fr[c]);
+          e = df_add(e, dflt{-xb.h, -xb.l});
+          dflt rq = df_mul(df_of(fr[3 + 3 * c]), qd[0]);
+          rq = df_add(rq, df_mul(df_of(fr[4 + 3 * c]), qd[1]));
+          rq = df_add(rq, df_mul(df_of(fr[5 + 3 * c]), qd[2]));
+          e = df_add(e, dflt{-rq.h, -rq.l});
+          if (per[c]) {
+            const float half = 0.5f * (float)n3[c];
+            if (e.h > half || (e.h == half && e.l > 0.0f)) e = df_add(dflt{e.h - (float)n3[c], 0.0f}, dflt{e.l, 0.0f});
+            else if (e.h < -half || (e.h == -half && e.l < 0.0f)) e = df_add(dflt{e.h + (float)n3[c], 0.0f}, dflt{e.l, 0.0f});
+          }
+          F[c] += (C)(-kf * (e.h + e.l)) + (C)d.rigid.frep[3 * body + c] * (C)inv_nf;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double site = fr[c] + fr[3 + 3 * c] * q[0] + fr[4 + 3 * c] * q[1] + fr[5 + 3 * c] * q[2];
+          const double dev = min_image(r1[c] - site, n3[c], per[c]);
           F[c] += (C)(-d.rigid.k * dev + d.rigid.frep[3 * body + c] * inv_n);
+        }
       }
     }
     if (d.fint_out) {
@@ -373,13 +458,13 @@ __device__ __forceinline__ void drift_one(const PartArgs& __restrict__ p,
   if (d.vel_out)
     for (int c = 0; c < 3; ++c) d.vel_out[c * M + i] = v[c];
   if (d.write_key) {
-    d.key_out[i] = key_of(g, r2[0], r2[1], r2[2]);
+    d.key_out[i] = F32 ? key_of_f(g, r2[0], r2[1], r2[2]) : key_of(g, r2[0], r2[1], r2[2]);
     d.idx_out[i] = (uint32_t)i;
     if (i == 0 && d.clear_flags) {       // the flags of the previous step
       d.clear_flags[0] = 0;
       d.clear_flags[1] = 0;
     }
-    if (d.home && !near_home(g, d.home[i], r2)) *d.need = 1;
+    if (d.home && !(F32 ? near_home_f(g, d.home[i], r2) : near_home(g, d.home[i], r2))) *d.need = 1;
   }
 }
 
@@ -437,6 +522,7 @@ __device__ inline void block_sum(double (&v)[NV], double (*sh)[FRAME_THREADS]) {
 // markers: with m = mean(d), X = r0 + m and A = sum d q^T - m (sum q)^T
 // (the offsets d are below two radii, so no large coordinate enters the
 // sums).
+template <bool DF>
 __global__ void __launch_bounds__(FRAME_THREADS)
 rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
   __shared__ double sh[15][FRAME_THREADS];
@@ -450,10 +536,73 @@ rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
   double r0[3];
   for (int c = 0; c < 3; ++c) {
     const double v = d.vel_in[c * M + f];
-    r0[c] = (d.pos_in[c * M + f] + d.dt_pre0 * v) + d.dt_pre * v;
+    r0[c] = DF ? d.pos_in[c * M + f] + (d.dt_pre0 + d.dt_pre) * v
+               : (d.pos_in[c * M + f] + d.dt_pre0 * v) + d.dt_pre * v;
   }
   // sums: d (3), q (3), d q^T (9)
   double acc[15];
+  if constexpr (DF) {
+    // FP32 compute: the same sums in double-float arithmetic on the FP32
+    // pipe.  d = (x_i - x_0) + dt (v_i - v_0): the position difference from
+    // the float splits of the FP64 positions (TwoSum of the highs), the
+    // velocity term in float (|dt (v_i - v_0)| << 1, float rounding of v
+    // adds below 2^-24 |v| dt to it); the minimum image subtracts n exactly.
+    const float dtf = (float)(d.dt_pre0 + d.dt_pre);
+    dflt x0[3];
+    float v0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x0[c] = df_of(d.pos_in[c * M + f]);
+      float vl;
+      split_df(d.vel_in[c * M + f], v0[c], vl);
+    }
+    dflt sd[15];
+#pragma unroll
+    for (int v = 0; v < 15; ++v) sd[v] = dflt{0.0f, 0.0f};
+    for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
+      const long long i = f + k;
+      dflt dv[3], q[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dflt xi = df_of(d.pos_in[c * M + i]);
+        float vh, vl;
+        split_df(d.vel_in[c * M + i], vh, vl);
+        dflt e = df_add(xi, dflt{-x0[c].h, -x0[c].l});
+        e = df_add(e, dflt{dtf * (vh - v0[c]), 0.0f});
+        if (per[c]) {
+          const float half = 0.5f * (float)n3[c];
+          if (e.h > half || (e.h == half && e.l > 0.0f)) e = df_add(dflt{e.h - (float)n3[c], 0.0f}, dflt{e.l, 0.0f});
+          else if (e.h < -half || (e.h == -half && e.l < 0.0f)) e = df_add(dflt{e.h + (float)n3[c], 0.0f}, dflt{e.l, 0.0f});
+        }
+        dv[c] = e;
+        q[c] = df_of(rg.ref[c * M + i]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sd[c] = df_add(sd[c], dv[c]);
+        sd[3 + c] = df_add(sd[3 + c], q[c]);
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sd[6 + 3 * r + c] = df_add(sd[6 + 3 * r + c], df_mul(dv[r], q[c]));
+    }
+    // block sum in double-float (the scratch as float pairs)
+    float2 (*sh2)[FRAME_THREADS] = reinterpret_cast<float2 (*)[FRAME_THREADS]>(sh);
+    for (int v = 0; v < 15; ++v) sh2[v][threadIdx.x] = make_float2(sd[v].h, sd[v].l);
+    __syncthreads();
+    for (int w = FRAME_THREADS / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w)
+        for (int v = 0; v < 15; ++v) {
+          const float2 a2 = sh2[v][threadIdx.x], b2 = sh2[v][threadIdx.x + w];
+          const dflt r = df_add(dflt{a2.x, a2.y}, dflt{b2.x, b2.y});
+          sh2[v][threadIdx.x] = make_float2(r.h, r.l);
+        }
+      __syncthreads();
+    }
+    for (int v = 0; v < 15; ++v) acc[v] = (double)sh2[v][0].x + (double)sh2[v][0].y;
+    __syncthreads();
+  } else {
 #pragma unroll
   for (int v = 0; v < 15; ++v) acc[v] = 0.0;
   for (int k = threadIdx.x; k < cnt; k += FRAME_THREADS) {
@@ -477,6 +626,7 @@ rigid_frames_kernel(const PartArgs p, const DriftArgs d) {
       for (int c = 0; c < 3; ++c) acc[6 + 3 * r + c] += dv[r] * q[c];
   }
   block_sum<15>(acc, sh);
+  }
   const double m[3] = {acc[0] / cnt, acc[1] / cnt, acc[2] / cnt};
   const double X[3] = {r0[0] + m[0], r0[1] + m[1], r0[2] + m[2]};
   double A[9];

@@ -52,7 +52,8 @@ inline int device_slot(int* sms) {
 
 void launch_rigid_frames(const PartArgs& p, const DriftArgs& d, cudaStream_t s) {
   if (d.rigid.nbodies <= 0) return;
-  rigid_frames_kernel<<<d.rigid.nbodies, FRAME_THREADS, 0, s>>>(p, d);
+  if (p.storage == ST_F64) rigid_frames_kernel<false><<<d.rigid.nbodies, FRAME_THREADS, 0, s>>>(p, d);
+  else rigid_frames_kernel<true><<<d.rigid.nbodies, FRAME_THREADS, 0, s>>>(p, d);
   const int rb = REPULSION_THREADS / 32;
   rigid_repulsion_kernel<<<(d.rigid.nbodies + rb - 1) / rb, REPULSION_THREADS, 0, s>>>(p, d.rigid);
 }
