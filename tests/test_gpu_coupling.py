@@ -333,16 +333,25 @@ def test_single_block_and_multi_pass_sorts(M):
 def test_long_axis_beyond_16_bit_stencil_bases(storage, stencil):
     """A 40000 x 4 x 4 box: stencil bases beyond 2^15 along x (kept as
     21-bit fields), markers on an exact node, at half-integers, around 2^15
-    and across the periodic face, against the oracle.  The 4-cell axes fold
-    the stencils onto themselves."""
+    and across the periodic face, and bonds at their rest length at large
+    coordinates (with FP32 compute the bond vector and |d|^2 - r0^2 are
+    formed in double-float arithmetic from the FP64 positions; positions
+    rounded to FP32, 0.004 apart at 37 000, would move the bond forces far
+    beyond the 1e-7 bound), against the oracle.  The 4-cell axes fold the
+    stencils onto themselves."""
     require_cuda()
     shape = (4, 4, 40000)
     fbar0 = synth.random_populations(shape, seed=3, amp=1e-3)
     pos = np.array([[0.0, 1.3, 2.2], [39999.5, 2.0, 0.5], [39999.9, 3.7, 1.1],
                     [20000.25, 0.2, 3.9], [32767.5, 1.5, 2.5], [32768.5, 2.5, 1.5],
-                    [39000.0, 1.0, 1.0]])
+                    [39000.0, 1.0, 1.0],
+                    # a chain at its rest length far from the origin (and one
+                    # bond across the periodic face): |d|^2 - r0^2 starts at 0
+                    [37000.3, 2.1, 1.7], [37001.3, 2.1, 1.7], [37002.3, 2.1, 1.7],
+                    [39999.6, 0.4, 3.0], [0.6, 0.4, 3.0]])
     rng = np.random.default_rng(7)
-    parts = dict(pos=pos, vel=0.01 * rng.standard_normal(pos.shape), mass=np.ones(len(pos)))
+    parts = dict(pos=pos, vel=0.01 * rng.standard_normal(pos.shape), mass=np.ones(len(pos)),
+                 bonds=np.array([[7, 8], [8, 9], [10, 11]]), bond_k=0.3, bond_r0=1.0)
     box, sm = make_pair(shape, fbar0, coll="mrt", tau=0.8, g=(1e-5, 0, 0), storage=storage,
                         kind="fc", stencil=stencil, gamma=1.0, parts=parts)
     tol = 1e-11 if storage == "f64" else 1e-7
