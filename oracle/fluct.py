@@ -135,18 +135,22 @@ def relax_fluct(f, gam, phi, noise):
     return feq + np.tensordot(np.linalg.inv(L.MRT_E), m, axes=([1], [0]))
 
 
-def _noise(shape, step, stream, seed):
+def _noise(shape, step, stream, seed, cells=None):
     """Standard normal kicks for the 19 moments of every cell (the four
-    conserved ones are drawn and multiplied by phi = 0)."""
+    conserved ones are drawn and multiplied by phi = 0).  cells: the flat
+    cell indices x + nx (y + ny z) that number the counters (default: the
+    cells of this array in order; a block cut out of a larger box passes the
+    indices the cells have there)."""
     ncell = int(np.prod(shape))
-    r = gaussians(np.arange(ncell), step, stream, L.Q, seed)
+    idx = np.arange(ncell) if cells is None else np.asarray(cells).reshape(-1)
+    r = gaussians(idx, step, stream, L.Q, seed)
     return r.reshape((L.Q,) + tuple(shape))
 
 
-def step_recombined_fluct(fbar, Fa, Fb, p, kT, seed, step, printed=False):
+def step_recombined_fluct(fbar, Fa, Fb, p, kT, seed, step, printed=False, cells=None):
     """(O2) with thermal fluctuations: fbar_new(x + c) = f^eq(rho, u1) +
     E^-1 [gamma m^neq(u0) + sqrt(rho) phi r] (one kick of the full-step
-    amplitude per step)."""
+    amplitude per step).  cells: as for _noise."""
     shape = fbar.shape[1:]
     g = p.g.reshape(3, 1, 1, 1)
     rho = L.density(fbar)
@@ -159,7 +163,7 @@ def step_recombined_fluct(fbar, Fa, Fb, p, kT, seed, step, printed=False):
     phi = amplitudes(gam, kT, printed)
     m = np.tensordot(L.MRT_E, fbar - L.equilibrium(rho, u0), axes=([1], [0]))
     m = gam.reshape((L.Q, 1, 1, 1)) * m + np.sqrt(rho) * phi.reshape((L.Q, 1, 1, 1)) * \
-        _noise(shape, step, 0, seed)
+        _noise(shape, step, 0, seed, cells)
     post = np.tensordot(np.linalg.inv(L.MRT_E), m, axes=([1], [0]))
     return OL.stream(L.equilibrium(rho, u1) + post, p)
 

@@ -76,6 +76,46 @@ def test_lb_step_256_on_sampled_cells(tau):
     assert err < 1e-7, err
 
 
+def test_thermal_lb_step_256_on_sampled_cells():
+    """The fused thermal step (Eq. [mrt-fluct]) at the full size in the
+    bench's launch configuration: 400 sampled cells (the eight corners
+    among them) against the oracle's fluctuating step of their 3^3
+    neighbourhoods, each cell's kicks drawn from the Philox counter of its
+    flat index in the full box."""
+    require_cuda()
+    from paper_1406_2211_gb300 import lbc
+    from oracle import fluct as OF
+    c = dict(synth.config(NAME), tau=0.8)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    kT, seed = 1e-5, 2014
+    box = lbc.Box(_lattice(lbc, c), _coupling(lbc, c), max_particles=1)
+    box.autotune()
+    box.set_populations(synth.random_populations(shape, seed=46, amp=1e-3))
+    f0 = box.get_populations()
+    box.set_thermal(kT, seed)
+    box.step(1)                                   # the first step after the seed: counter 0
+    f1 = box.get_populations()
+    box.close()
+    p = OL.LBParams(collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                    body_force=c["body_force"])
+    rng = np.random.default_rng(47)
+    cells = rng.integers(0, [nz, ny, nx], size=(400, 3))
+    corners = [[z, y, x] for z in (0, nz - 1) for y in (0, ny - 1) for x in (0, nx - 1)]
+    cells[:len(corners)] = corners
+    err = 0.0
+    for z, y, x in cells:
+        iz = (z + np.arange(-1, 2)) % nz
+        iy = (y + np.arange(-1, 2)) % ny
+        ix = (x + np.arange(-1, 2)) % nx
+        loc = f0[:, iz][:, :, iy][:, :, :, ix]
+        flat = (iz[:, None, None] * ny + iy[None, :, None]) * nx + ix[None, None, :]
+        out = OF.step_recombined_fluct(loc, None, None, p, kT, seed, 0, cells=flat)[:, 1, 1, 1]
+        err = max(err, float(np.abs(out - f1[:, z, y, x]).max()))
+    # FP32 arithmetic on deviations of 1e-3 and kicks of about 1e-2 x sqrt(mu)
+    assert err < 1e-7, err
+
+
 def test_bead_chain_workload_256_mass_and_momentum():
     require_cuda()
     from paper_1406_2211_gb300 import lbc
