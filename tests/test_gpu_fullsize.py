@@ -36,15 +36,21 @@ def _coupling(lbc, c):
                              substeps=c["substeps"])
 
 
-@pytest.mark.parametrize("tau", [1.0, 0.8])
-def test_lb_step_256_on_sampled_cells(tau):
+@pytest.mark.parametrize("tau,storage", [(1.0, "f32"), (0.8, "f32"), (1.0, "f16dev"),
+                                         (0.8, "bf16dev")])
+def test_lb_step_256_on_sampled_cells(tau, storage):
     """tau = 1 is the workload's setting, where MRT with fully relaxed ghosts
     has every non-conserved eigenvalue 1 - lambda = 0 and the step is
     f^eq(u1) (the same as BGK at tau = 1); tau = 0.8 relaxes the stress with
-    eigenvalue -0.25, so the kernel's non-equilibrium path is checked too."""
+    eigenvalue -0.25, so the kernel's non-equilibrium path is checked too.
+    The 16-bit forms run the two-cell kernel of the bench's storage forms;
+    each stored value is rounded stochastically to one of its two 16-bit
+    neighbours, so their bound adds one spacing (FP16: 2^-10, BF16: 2^-7 of
+    the scaled deviation, twice that below it)."""
     require_cuda()
     from paper_1406_2211_gb300 import lbc
-    c = dict(synth.config(NAME), tau=tau)
+    from oracle import lattice as OLat
+    c = dict(synth.config(NAME), tau=tau, storage=storage)
     nx, ny, nz = c["box"]
     shape = (nz, ny, nx)
     # force fields allocated, no particle set: the step is the LB step with
@@ -64,7 +70,9 @@ def test_lb_step_256_on_sampled_cells(tau):
     cells = rng.integers(0, [nz, ny, nx], size=(400, 3))
     corners = [[z, y, x] for z in (0, nz - 1) for y in (0, ny - 1) for x in (0, nx - 1)]
     cells[:len(corners)] = corners                # periodic wrap on every face
-    err = 0.0
+    sp = {"f32": 0.0, "f16dev": 2.0 ** -9, "bf16dev": 2.0 ** -6}[storage]
+    w0 = (OLat.W * c["rho0"]).reshape(-1)
+    worst = 0.0
     for z, y, x in cells:
         iz = (z + np.arange(-1, 2)) % nz
         iy = (y + np.arange(-1, 2)) % ny
@@ -72,8 +80,9 @@ def test_lb_step_256_on_sampled_cells(tau):
         loc = f0[:, iz][:, :, iy][:, :, :, ix]
         Floc = Fa[:, iz][:, :, iy][:, :, :, ix]
         out = OL.step_recombined(loc, Floc, None, p)[:, 1, 1, 1]
-        err = max(err, float(np.abs(out - f1[:, z, y, x]).max()))
-    assert err < 1e-7, err
+        tol = 1e-7 + sp * np.abs(out - w0)
+        worst = max(worst, float((np.abs(out - f1[:, z, y, x]) / tol).max()))
+    assert worst <= 1.0, worst
 
 
 def test_thermal_lb_step_256_on_sampled_cells():
