@@ -125,6 +125,50 @@ def test_thermal_lb_step_256_on_sampled_cells():
     assert err < 1e-7, err
 
 
+def test_stress_epilogue_256_on_sampled_cells():
+    """The stress epilogue (Eq. [viscstress]) at the full size in the bench's
+    launch configuration (tau = 0.8, so the stress relaxes): sampled cells
+    of the written sigma against oracle.lb.viscous_stress of the state the
+    step collided, and the step's populations unchanged by the epilogue on
+    the same sampled cells against the plain step's oracle."""
+    require_cuda()
+    import torch
+    from paper_1406_2211_gb300 import lbc
+    c = dict(synth.config(NAME), tau=0.8)
+    nx, ny, nz = c["box"]
+    shape = (nz, ny, nx)
+    box = lbc.Box(_lattice(lbc, c), _coupling(lbc, c), max_particles=1)
+    box.autotune()
+    box.set_populations(synth.random_populations(shape, seed=48, amp=1e-3))
+    f0 = box.get_populations()
+    sig = box.stress_output()
+    box.step(1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(49)
+    cells = rng.integers(0, [nz, ny, nx], size=(400, 3))
+    got = sig.cpu().numpy()
+    f1 = box.get_populations()
+    box.stress_output(False)
+    box.close()
+    p = OL.LBParams(collision=c["collision"], tau=c["tau"], rho0=c["rho0"],
+                    body_force=c["body_force"])
+    comp = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2))
+    worst, worst_f = 0.0, 0.0
+    for z, y, x in cells:
+        ref = OL.viscous_stress(f0[:, z:z + 1, y:y + 1, x:x + 1], p)[:, :, 0, 0, 0]
+        for k, (a, b) in enumerate(comp):
+            worst = max(worst, abs(float(got[k, z, y, x]) - ref[a, b]))
+        iz = (z + np.arange(-1, 2)) % nz
+        iy = (y + np.arange(-1, 2)) % ny
+        ix = (x + np.arange(-1, 2)) % nx
+        loc = f0[:, iz][:, :, iy][:, :, :, ix]
+        out = OL.step_recombined(loc, None, None, p)[:, 1, 1, 1]
+        worst_f = max(worst_f, float(np.abs(out - f1[:, z, y, x]).max()))
+    # FP32 sums of 19 deviations of 1e-3
+    assert worst < 1e-8, worst
+    assert worst_f < 1e-7, worst_f
+
+
 def test_bead_chain_workload_256_mass_and_momentum():
     require_cuda()
     from paper_1406_2211_gb300 import lbc
